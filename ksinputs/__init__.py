@@ -1,0 +1,179 @@
+"""Seeded synthetic Kohn-Sham matrices (H, S) shared by the tests, the oracle checks and
+the benchmark. This module holds input construction only: none of the solver's
+arithmetic (no factorisation, no eigensolver, no occupation, no density matrix).
+
+The paper's workloads are FHI-aims / DGDFT graphene Hamiltonians (arXiv:1705.11191,
+Table 1) that are not available here; these decaying random matrices stand in for
+them with the same shape: 8-15 basis functions per atom, an occupied fraction of 25 %
+(within the 10-40 % the paper quotes for localized basis sets, sec. 2) and a
+positive-definite overlap.
+
+Recipe (all draws from numpy's PCG64 ``default_rng(seed)`` in this order):
+  1. atom positions (1D chain: fixed spacing; 3D cluster: uniform in a cube, rejection
+     sampling for a 2 bohr minimum separation);
+  2. u  = rng.random((n, n))        -> S off-diagonal factors (upper triangle used);
+  3. hd = rng.uniform(-1, 0.5, n)  -> H diagonal (onsite energies, Ha);
+  4. g  = rng.standard_normal((n, n)) -> H off-diagonal noise (upper triangle used).
+  With d_ij the distance between the atoms carrying basis functions i and j
+  (0 on the same atom):
+     O_ij = 0.3 exp(-d_ij/1.5) u_ij               (i != j, mirrored from i < j)
+     H_ij = -0.5 exp(-d_ij/1.2) (1 + 0.1 g_ij)    (i != j, mirrored from i < j)
+     S    = I + alpha O, alpha = 1, or, when lambda_min(I + O) < tau,
+            alpha = (1 - tau) / (-lambda_min(O)) so that lambda_min(S) = tau exactly.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+__all__ = ["Problem", "chain_positions", "cluster_positions", "build", "config",
+           "basis_atoms", "CONFIGS"]
+
+
+@dataclasses.dataclass
+class Problem:
+    h: np.ndarray          # (n, n) float64, column-major (Fortran order)
+    s: np.ndarray          # (n, n) float64, column-major
+    n_electron: float
+    n_state: int
+    name: str
+    lambda_min_s: float
+
+    @property
+    def n(self) -> int:
+        return self.h.shape[0]
+
+
+def chain_positions(n_atoms: int, spacing: float = 2.0) -> np.ndarray:
+    x = np.zeros((n_atoms, 3))
+    x[:, 0] = spacing * np.arange(n_atoms)
+    return x
+
+
+def cluster_positions(rng: np.random.Generator, n_atoms: int, density: float = 0.01,
+                      min_sep: float = 2.0) -> np.ndarray:
+    side = (n_atoms / density) ** (1.0 / 3.0)
+    pos = np.zeros((n_atoms, 3))
+    k = 0
+    while k < n_atoms:
+        p = rng.random(3) * side
+        if k == 0 or np.min(np.sum((pos[:k] - p) ** 2, axis=1)) >= min_sep * min_sep:
+            pos[k] = p
+            k += 1
+    return pos
+
+
+def basis_atoms(n: int, per_atom: int) -> np.ndarray:
+    """Atom index of each basis function: per_atom functions per atom, the last atom
+    carrying the remainder."""
+    return np.arange(n) // per_atom
+
+
+def _lambda_min(o: np.ndarray) -> float:
+    n = o.shape[0]
+    if n <= 2048:
+        return float(np.linalg.eigvalsh(o)[0])
+    from scipy.sparse.linalg import eigsh
+    w = eigsh(o, k=1, which="SA", tol=1e-12, return_eigenvectors=False)
+    return float(w[0])
+
+
+def build(rng: np.random.Generator, pos: np.ndarray, n: int, per_atom: int,
+          tau: float = 1e-2, force_tau: bool = False):
+    """Returns (H, S, lambda_min(S)) for the atom positions and basis layout."""
+    atom = basis_atoms(n, per_atom)
+    xyz = pos[atom]                                     # (n, 3)
+    d = np.zeros((n, n))
+    for c in range(3):
+        diff = xyz[:, c][:, None] - xyz[:, c][None, :]
+        d += diff * diff
+    np.sqrt(d, out=d)
+    u = rng.random((n, n))
+    iu = np.triu_indices(n, 1) if n <= 4096 else None
+    o = np.exp(-d / 1.5)
+    o *= 0.3
+    o *= u
+    del u
+    _mirror_upper(o)
+    np.fill_diagonal(o, 0.0)
+    hd = rng.uniform(-1.0, 0.5, n)
+    g = rng.standard_normal((n, n))
+    h = np.exp(-d / 1.2)
+    h *= -0.5
+    g *= 0.1
+    g += 1.0
+    h *= g
+    del g, d
+    _mirror_upper(h)
+    h[np.diag_indices(n)] = hd
+    lam_o = _lambda_min(o)
+    alpha = 1.0
+    if force_tau or 1.0 + lam_o < tau:
+        alpha = (1.0 - tau) / (-lam_o)
+    s = o
+    s *= alpha
+    s[np.diag_indices(n)] = 1.0
+    del iu
+    return (np.asfortranarray(h), np.asfortranarray(s), 1.0 + alpha * lam_o)
+
+
+def _mirror_upper(a: np.ndarray, block: int = 2048) -> None:
+    """a[j, i] = a[i, j] for i < j (the upper triangle is the authoritative draw)."""
+    n = a.shape[0]
+    for r0 in range(0, n, block):
+        r1 = min(n, r0 + block)
+        for c0 in range(r0, n, block):
+            c1 = min(n, c0 + block)
+            blk = a[r0:r1, c0:c1]
+            if c0 == r0:
+                up = np.triu(blk, 1)
+                a[r0:r1, c0:c1] = up + up.T + np.diag(np.diag(blk))
+            else:
+                a[c0:c1, r0:r1] = blk.T
+
+
+# (name, geometry, n, per_atom, n_electron, n_state, seed)
+CONFIGS = {
+    0: dict(name="chain-n512", geometry="chain", n=512, per_atom=8, n_atoms=64,
+            n_electron=256.0, n_state=512, seed=0),
+    1: dict(name="cluster3d-n8192", geometry="cluster", n=8192, per_atom=15, n_atoms=547,
+            n_electron=2048.0, n_state=1024, seed=1),
+    2: dict(name="cluster3d-n16384", geometry="cluster", n=16384, per_atom=15,
+            n_atoms=1093, n_electron=4096.0, n_state=2048, seed=2),
+}
+
+
+def cluster_problem(n: int, seed: int, per_atom: int = 15, tau: float = 1e-2,
+                    force_tau: bool = False, n_state: int | None = None,
+                    n_electron: float | None = None) -> Problem:
+    """3D-cluster construction at any size n (used for the small parity cases)."""
+    rng = np.random.default_rng(seed)
+    n_atoms = math.ceil(n / per_atom)
+    pos = cluster_positions(rng, n_atoms)
+    h, s, lam = build(rng, pos, n, per_atom, tau=tau, force_tau=force_tau)
+    ne = float(n // 4) if n_electron is None else float(n_electron)
+    ns = max(1, int(math.ceil(ne / 2))) if n_state is None else int(n_state)
+    return Problem(h, s, ne, ns, f"cluster3d-n{n}-seed{seed}", lam)
+
+
+def chain_problem(n_atoms: int, per_atom: int, seed: int, n_electron: float,
+                  n_state: int, tau: float = 1e-2) -> Problem:
+    rng = np.random.default_rng(seed)
+    n = n_atoms * per_atom
+    pos = chain_positions(n_atoms)
+    h, s, lam = build(rng, pos, n, per_atom, tau=tau)
+    return Problem(h, s, float(n_electron), int(n_state), f"chain-n{n}-seed{seed}", lam)
+
+
+def config(i: int, tau: float | None = None) -> Problem:
+    c = CONFIGS[i]
+    if c["geometry"] == "chain":
+        return chain_problem(c["n_atoms"], c["per_atom"], c["seed"], c["n_electron"],
+                             c["n_state"])
+    rng = np.random.default_rng(c["seed"])
+    pos = cluster_positions(rng, c["n_atoms"])
+    h, s, lam = build(rng, pos, c["n"], c["per_atom"],
+                      tau=1e-2 if tau is None else tau, force_tau=tau is not None)
+    return Problem(h, s, c["n_electron"], c["n_state"], c["name"], lam)

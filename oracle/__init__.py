@@ -1,0 +1,193 @@
+"""FP64 CPU oracle for the dense Kohn-Sham solver path (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+import this package. The product library (``paper_1705_11191_gb300``) never imports,
+links or calls it, and the two share no code.
+
+The arithmetic lives in ``oracle.c`` (plain C, binary64, column-major); this module
+compiles it with gcc on first use and wraps it with ctypes. Arrays are passed as numpy
+float64 arrays in Fortran (column-major) order.
+
+Each routine follows arXiv:1705.11191 (ELSI):
+  cholesky        Eq. 8 (S = L L^*)
+  standard_form   Eq. 9 (H~ = L^{-1} H L^{-*})
+  jacobi          eigendecomposition of H~ by cyclic Jacobi (the plain definition of
+                  the eigenpairs that Eqs. 10-11 reach by two-stage tridiagonalisation)
+  back_substitute Eq. 9 (c = L^{-*} c~)
+  occupation      sec. 4.4 (elsi_dm_real): bisection for mu, Eqs. 14-15, 17-18, and
+                  the exact-charge correction
+  weighted_outer  Eq. 7 (density matrix) and its energy-weighted form W
+  solve           the whole path
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, OpenMP). Returns the library path."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i, d = ctypes.c_int, ctypes.c_double
+            lib.orc_cholesky.argtypes = [i, _dp, _dp]
+            lib.orc_cholesky.restype = i
+            lib.orc_standard_form.argtypes = [i, _dp, _dp, _dp]
+            lib.orc_standard_form.restype = None
+            lib.orc_jacobi.argtypes = [i, _dp, _dp, _dp, i]
+            lib.orc_jacobi.restype = i
+            lib.orc_sort_eigenpairs.argtypes = [i, _dp, _dp]
+            lib.orc_sort_eigenpairs.restype = None
+            lib.orc_back_substitute.argtypes = [i, i, _dp, _dp, _dp]
+            lib.orc_back_substitute.restype = None
+            lib.orc_occupation.argtypes = [i, _dp, d, i, d, d, i, _dp, _dp]
+            lib.orc_occupation.restype = i
+            lib.orc_weighted_outer.argtypes = [i, i, _dp, _dp, _dp]
+            lib.orc_weighted_outer.restype = None
+            lib.orc_solve.argtypes = [i, i, _dp, _dp, i, d, i, d, d, i,
+                                      _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+            lib.orc_solve.restype = i
+            lib.orc_num_threads.argtypes = []
+            lib.orc_num_threads.restype = i
+            _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def cholesky(s):
+    s = _f64(s)
+    n = s.shape[0]
+    l = np.zeros((n, n), order="F")
+    rc = _load().orc_cholesky(n, _ptr(s), _ptr(l))
+    if rc:
+        raise OracleError(f"S not positive definite at pivot {rc - 1}")
+    return l
+
+
+def standard_form(h, l):
+    h, l = _f64(h), _f64(l)
+    n = h.shape[0]
+    ht = np.zeros((n, n), order="F")
+    _load().orc_standard_form(n, _ptr(h), _ptr(l), _ptr(ht))
+    return ht
+
+
+def jacobi(a, max_sweeps: int = 60, sort: bool = True):
+    """Eigenpairs of symmetric a by cyclic Jacobi. Returns (w, V, sweeps)."""
+    a = np.array(_f64(a), order="F", copy=True)
+    n = a.shape[0]
+    w = np.zeros(n)
+    v = np.zeros((n, n), order="F")
+    sweeps = _load().orc_jacobi(n, _ptr(a), _ptr(w), _ptr(v), max_sweeps)
+    if sweeps < 0:
+        raise OracleError("Jacobi did not converge")
+    if sort:
+        _load().orc_sort_eigenpairs(n, _ptr(w), _ptr(v))
+    return w, v, sweeps
+
+
+def back_substitute(l, vt, k: int | None = None):
+    l, vt = _f64(l), _f64(vt)
+    n = l.shape[0]
+    k = vt.shape[1] if k is None else k
+    c = np.zeros((n, k), order="F")
+    _load().orc_back_substitute(n, k, _ptr(l), _ptr(vt), _ptr(c))
+    return c
+
+
+SCHEME_INTEGER, SCHEME_GAUSSIAN, SCHEME_FERMI = 0, 1, 2
+
+
+def occupation(eps, n_el: float, scheme: int = SCHEME_INTEGER, kt: float = 0.0,
+               occ_accuracy: float = 1e-12, mu_max_steps: int = 200):
+    """Returns (f, mu) for the ascending eigenvalues eps."""
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    k = eps.shape[0]
+    f = np.zeros(k)
+    mu = ctypes.c_double(0.0)
+    rc = _load().orc_occupation(k, _ptr(eps), float(n_el), int(scheme), float(kt),
+                                float(occ_accuracy), int(mu_max_steps), _ptr(f),
+                                ctypes.byref(mu))
+    if rc:
+        raise OracleError("occupation failed")
+    return f, mu.value
+
+
+def weighted_outer(c, w):
+    """sum_l w_l c_l c_l^T over the columns of c."""
+    c = _f64(c)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n, k = c.shape
+    d = np.zeros((n, n), order="F")
+    _load().orc_weighted_outer(n, k, _ptr(c), _ptr(w), _ptr(d))
+    return d
+
+
+def solve(h, s, n_state: int, n_el: float, *, unit_ovlp: bool = False,
+          scheme: int = SCHEME_INTEGER, kt: float = 0.0, occ_accuracy: float = 1e-12,
+          mu_max_steps: int = 200, want_pw: bool = True):
+    """Whole path. Returns dict(eval (n), C (n x n_state), f, mu, P, W, energy)."""
+    h = _f64(h)
+    n = h.shape[0]
+    s = _f64(s) if s is not None else np.eye(n, order="F")
+    k = int(n_state)
+    ev = np.zeros(n)
+    c = np.zeros((n, k), order="F")
+    f = np.zeros(k)
+    p = np.zeros((n, n), order="F") if want_pw else None
+    w = np.zeros((n, n), order="F") if want_pw else None
+    e = ctypes.c_double(0.0)
+    mu = ctypes.c_double(0.0)
+    null = ctypes.cast(None, _dp)
+    rc = _load().orc_solve(n, k, _ptr(h), _ptr(s), int(bool(unit_ovlp)), float(n_el),
+                           int(scheme), float(kt), float(occ_accuracy), int(mu_max_steps),
+                           _ptr(ev), _ptr(c), _ptr(f),
+                           _ptr(p) if want_pw else null, _ptr(w) if want_pw else null,
+                           ctypes.byref(e), ctypes.byref(mu))
+    if rc > 0:
+        raise OracleError(f"S not positive definite at pivot {rc - 1}")
+    if rc == -1:
+        raise OracleError("Jacobi did not converge")
+    if rc == -2:
+        raise OracleError("occupation failed")
+    return dict(eval=ev, C=c, f=f, mu=mu.value, P=p, W=w, energy=e.value)
