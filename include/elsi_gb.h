@@ -1,0 +1,137 @@
+/*
+ * elsi_gb.h - C ABI of the single-GPU (GB300, sm_103a) dense Kohn-Sham solver.
+ *
+ * The library solves the generalized Kohn-Sham eigenproblem H c = eps S c
+ * (arXiv:1705.11191, Eqs. 5-6, sec. 2) along the route ELSI drives through ELPA
+ * (sec. 3.1, Eqs. 8-11): Cholesky S = L L^T, standard form H~ = L^{-1} H L^{-T},
+ * two-stage reduction full -> band -> tridiagonal, tridiagonal eigensolver,
+ * back-transformation of the eigenvectors through both stages and L^{-T}; then the
+ * chemical potential and occupations (sec. 4.4, Eqs. 14-15, 17-18), the density
+ * matrix P = sum_l f_l c_l c_l^T (Eq. 7), the energy-weighted density matrix
+ * W = sum_l f_l eps_l c_l c_l^T and the band energy E = sum_l f_l eps_l.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are real symmetric, n_basis x n_basis, binary64, COLUMN-MAJOR with leading
+ *    dimension n_basis, and BOTH triangles must be filled (the BLACS_DENSE reading of
+ *    sec. 4.2 on one GPU). Eigenvector l is the contiguous column evec[l*n_basis ...].
+ *  - Unless a name ends in _host, every array argument is a DEVICE pointer on the
+ *    current CUDA device; scalars written back (energy, mu) are HOST pointers.
+ *    The caller owns all buffers; the handle owns its workspace and the cached
+ *    Cholesky factor.
+ *  - Work is enqueued on the handle's stream (elsi_set_stream; default: the legacy
+ *    default stream). Each solve synchronises that stream once at the end to read the
+ *    device status word, so results are valid when the call returns.
+ *  - Return value: ELSI_OK (0) or one of the ELSI_ERR_* codes below; a message is
+ *    available from elsi_get_last_error(h).
+ */
+#ifndef ELSI_GB_H
+#define ELSI_GB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define ELSI_OK 0
+#define ELSI_ERR_ARG 1          /* invalid argument (null pointer, bad size, bad enum) */
+#define ELSI_ERR_UNSUPPORTED 2  /* option of the paper not provided on one GPU */
+#define ELSI_ERR_NOT_PD 3       /* S not positive definite (failing pivot in aux) */
+#define ELSI_ERR_NONFINITE 4    /* NaN or Inf met in the input or an intermediate */
+#define ELSI_ERR_NO_CONVERGENCE 5 /* mu bisection or refinement did not converge */
+#define ELSI_ERR_TIMEOUT 6      /* a bounded device-side wait expired */
+#define ELSI_ERR_CUDA 7         /* a CUDA runtime call failed */
+#define ELSI_ERR_STATE 8        /* call order violated (e.g. get_edm before dm) */
+#define ELSI_ERR_NOMEM 9        /* workspace allocation failed */
+
+/* Enumerations of elsi_init (sec. 4.3). Only solver 1 (ELPA route), format 1
+ * (dense) and either parallel mode (both mean "one GPU, whole matrix") are accepted. */
+#define ELSI_SOLVER_ELPA 1
+#define ELSI_FORMAT_DENSE 1
+#define ELSI_MODE_MULTI_PROC 1
+#define ELSI_MODE_SINGLE_PROC 2
+
+/* Broadening schemes (elsi_customize_mu, sec. 4.5). 0 is this library's addition:
+ * integer (aufbau) occupation without broadening. 3 and 4 (Methfessel-Paxton) are
+ * named by the paper without a formula and return ELSI_ERR_UNSUPPORTED. */
+#define ELSI_OCC_INTEGER 0
+#define ELSI_OCC_GAUSSIAN 1
+#define ELSI_OCC_FERMI 2
+
+/* Arithmetic of the reduction and back-transformations. */
+#define ELSI_PREC_FP64 0        /* every stage in binary64 */
+#define ELSI_PREC_FP32_REFINE 1 /* binary32 reduction, then refinement to FP64 accuracy */
+
+typedef struct elsi_gb_handle_s *elsi_handle;
+
+/* elsi_init (sec. 4.3): create a handle for problems of size n_basis with n_state
+ * eigenstates and n_electron electrons. solver/format/parallel_mode as above.
+ * Requires 1 <= n_state <= n_basis and 0 <= n_electron <= 2*n_state. Allocates
+ * nothing on the GPU yet (workspace is sized at the first solve). */
+int elsi_init(elsi_handle *h, int solver, int matrix_storage_format, int parallel_mode,
+              int n_basis, int n_state, double n_electron);
+
+/* elsi_finalize (sec. 4.6): free the handle and its workspace; *h is set to NULL. */
+int elsi_finalize(elsi_handle *h);
+
+/* Customisation (sec. 4.5, elsi_customize / elsi_customize_mu / _elpa), per handle. */
+int elsi_set_overlap_is_unit(elsi_handle h, int overlap_is_unit);
+int elsi_set_broadening_scheme(elsi_handle h, int scheme);
+int elsi_set_broadening_width(elsi_handle h, double width); /* k_B T in Ha, > 0 */
+int elsi_set_occ_accuracy(elsi_handle h, double occ_accuracy);
+int elsi_set_mu_max_steps(elsi_handle h, int mu_max_steps);
+/* Additions of this library (no counterpart in the paper's keyword list): */
+int elsi_set_precision(elsi_handle h, int precision);      /* ELSI_PREC_* */
+int elsi_set_band_width(elsi_handle h, int band_width);    /* 8..128, multiple of 8 */
+int elsi_set_refine_max_iter(elsi_handle h, int iters);    /* 0..8 */
+int elsi_set_stream(elsi_handle h, void *cuda_stream);     /* cudaStream_t */
+/* Reuse the Cholesky factor of the previous call instead of factorising ovlp again
+ * (the reuse of L across an SCF cycle described in sec. 4.4). */
+int elsi_set_reuse_ovlp_factor(elsi_handle h, int reuse);
+
+/* elsi_ev_real (sec. 4.4): all n_basis eigenvalues (ascending) into eval[n_basis]
+ * and the n_state lowest eigenvectors (S-orthonormal columns) into
+ * evec[n_basis*n_state]. ham is used as workspace and destroyed on exit, as in the
+ * paper; ovlp is left unchanged (the handle keeps L instead of overwriting ovlp). */
+int elsi_ev_real(elsi_handle h, double *ham, const double *ovlp, double *eval, double *evec);
+
+/* elsi_dm_real (sec. 4.4): density matrix P (Eq. 7) into den_mat[n_basis^2] and the
+ * band energy sum_l f_l eps_l into *energy (host). The energy-weighted density matrix
+ * of the same call is kept in the handle for elsi_get_edm_real. ham is destroyed. */
+int elsi_dm_real(elsi_handle h, double *ham, const double *ovlp, double *den_mat,
+                 double *energy);
+
+/* Energy-weighted density matrix W = sum_l f_l eps_l c_l c_l^T of the last
+ * elsi_dm_real call (the paper names it only as a PEXSI output, sec. 4.4). */
+int elsi_get_edm_real(elsi_handle h, double *edm);
+
+/* Chemical potential (host scalar) and the n_state occupation numbers (device array)
+ * of the last elsi_dm_real call. */
+int elsi_get_mu(elsi_handle h, double *mu);
+int elsi_get_occ(elsi_handle h, double *occ);
+
+/* Same as elsi_dm_real + elsi_get_edm_real but with HOST (pageable or pinned)
+ * buffers: copies ham/ovlp in, solves, copies P and W out, on the handle's stream.
+ * ham_host is not modified. edm_host may be NULL. */
+int elsi_dm_real_host(elsi_handle h, const double *ham_host, const double *ovlp_host,
+                      double *den_mat_host, double *edm_host, double *energy);
+
+/* Per-stage device times (ms) of the last solve, in the order of
+ * elsi_stage_name(i), i < n; returns the number of stages written. */
+int elsi_get_stage_times(elsi_handle h, float *ms, int n);
+const char *elsi_stage_name(int i);
+
+/* Diagnostics of the last FP32_REFINE solve: refinement iterations used and the
+ * final max |(C^T S C - I)_ij| over the occupied block. */
+int elsi_get_refine_info(elsi_handle h, int *iters, double *orth_err);
+
+/* Message describing the last error on this handle ("" if none). */
+const char *elsi_get_last_error(elsi_handle h);
+
+/* Library version string. */
+const char *elsi_gb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELSI_GB_H */

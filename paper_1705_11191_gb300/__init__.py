@@ -1,0 +1,285 @@
+"""Single-GPU (GB300, sm_103a) dense Kohn-Sham solver: thin ctypes binding of the C ABI
+declared in ``include/elsi_gb.h`` (arXiv:1705.11191, the ELPA route driven by ELSI).
+
+Every step of a solve runs in the CUDA kernels of ``libelsi_gb.so``; this module only
+marshals arguments (torch CUDA tensors -> device pointers). There is no CPU fallback:
+if the library cannot be loaded, every call raises.
+
+Matrices are n x n float64 CUDA tensors. The library reads them column-major; for the
+symmetric H and S that is the same memory as torch's row-major layout. Eigenvectors
+come back as an (n, n_state) tensor whose column l is eigenvector l.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = ["load", "Handle", "ElsiError", "solve_dm", "solve_ev", "STAGES",
+           "SOLVER_ELPA", "FORMAT_DENSE", "MODE_SINGLE_PROC", "OCC_INTEGER",
+           "OCC_GAUSSIAN", "OCC_FERMI", "PREC_FP64", "PREC_FP32_REFINE", "LIB_PATH"]
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libelsi_gb.so")
+
+SOLVER_ELPA, FORMAT_DENSE, MODE_MULTI_PROC, MODE_SINGLE_PROC = 1, 1, 1, 2
+OCC_INTEGER, OCC_GAUSSIAN, OCC_FERMI = 0, 1, 2
+PREC_FP64, PREC_FP32_REFINE = 0, 1
+
+ERR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_UNSUPPORTED", 3: "ERR_NOT_PD",
+             4: "ERR_NONFINITE", 5: "ERR_NO_CONVERGENCE", 6: "ERR_TIMEOUT",
+             7: "ERR_CUDA", 8: "ERR_STATE", 9: "ERR_NOMEM"}
+
+_lib = None
+_lock = threading.Lock()
+_vp, _dp, _ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+
+
+class ElsiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _declare(lib):
+    i, d = ctypes.c_int, ctypes.c_double
+    H = _vp
+    sig = {
+        "elsi_init": ([ctypes.POINTER(_vp), i, i, i, i, i, d], i),
+        "elsi_finalize": ([ctypes.POINTER(_vp)], i),
+        "elsi_set_overlap_is_unit": ([H, i], i),
+        "elsi_set_broadening_scheme": ([H, i], i),
+        "elsi_set_broadening_width": ([H, d], i),
+        "elsi_set_occ_accuracy": ([H, d], i),
+        "elsi_set_mu_max_steps": ([H, i], i),
+        "elsi_set_precision": ([H, i], i),
+        "elsi_set_band_width": ([H, i], i),
+        "elsi_set_refine_max_iter": ([H, i], i),
+        "elsi_set_stream": ([H, _vp], i),
+        "elsi_set_reuse_ovlp_factor": ([H, i], i),
+        "elsi_ev_real": ([H, _vp, _vp, _vp, _vp], i),
+        "elsi_dm_real": ([H, _vp, _vp, _vp, _dp], i),
+        "elsi_get_edm_real": ([H, _vp], i),
+        "elsi_get_mu": ([H, _dp], i),
+        "elsi_get_occ": ([H, _vp], i),
+        "elsi_dm_real_host": ([H, _vp, _vp, _vp, _vp, _dp], i),
+        "elsi_get_stage_times": ([H, ctypes.POINTER(ctypes.c_float), i], i),
+        "elsi_stage_name": ([i], ctypes.c_char_p),
+        "elsi_get_refine_info": ([H, _ip, _dp], i),
+        "elsi_get_last_error": ([H], ctypes.c_char_p),
+        "elsi_gb_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+
+
+def load(path: str | None = None):
+    """Load libelsi_gb.so (building it first if it is missing). Raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                from . import build as _build
+                _build.build()
+            lib = ctypes.CDLL(p)
+            _declare(lib)
+            _lib = lib
+    return _lib
+
+
+def _n_stages(lib) -> int:
+    k = 0
+    while lib.elsi_stage_name(k):
+        k += 1
+    return k
+
+
+def stage_names() -> list[str]:
+    lib = load()
+    return [lib.elsi_stage_name(i).decode() for i in range(_n_stages(lib))]
+
+
+STAGES = None
+
+
+def _ptr(t) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+class Handle:
+    """An ELSI handle (sec. 4.1/4.3) bound to the current CUDA device and torch stream."""
+
+    def __init__(self, n_basis: int, n_state: int, n_electron: float, *,
+                 solver: int = SOLVER_ELPA, fmt: int = FORMAT_DENSE,
+                 mode: int = MODE_SINGLE_PROC, stream=None):
+        self._lib = load()
+        self._h = _vp()
+        rc = self._lib.elsi_init(ctypes.byref(self._h), solver, fmt, mode, int(n_basis),
+                                 int(n_state), float(n_electron))
+        if rc:
+            raise ElsiError(rc, "elsi_init")
+        self.n, self.n_state, self.n_electron = int(n_basis), int(n_state), float(n_electron)
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- lifetime
+    def close(self):
+        if self._h:
+            self._lib.elsi_finalize(ctypes.byref(self._h))
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc: int, what: str):
+        if rc:
+            msg = self._lib.elsi_get_last_error(self._h)
+            raise ElsiError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    # -- customisation
+    def set_overlap_is_unit(self, v: bool):
+        self._check(self._lib.elsi_set_overlap_is_unit(self._h, int(bool(v))), "set_overlap_is_unit")
+
+    def set_broadening(self, scheme: int, width: float | None = None):
+        self._check(self._lib.elsi_set_broadening_scheme(self._h, int(scheme)), "set_broadening_scheme")
+        if width is not None:
+            self._check(self._lib.elsi_set_broadening_width(self._h, float(width)), "set_broadening_width")
+
+    def set_occ_accuracy(self, a: float):
+        self._check(self._lib.elsi_set_occ_accuracy(self._h, float(a)), "set_occ_accuracy")
+
+    def set_mu_max_steps(self, s: int):
+        self._check(self._lib.elsi_set_mu_max_steps(self._h, int(s)), "set_mu_max_steps")
+
+    def set_precision(self, p: int):
+        self._check(self._lib.elsi_set_precision(self._h, int(p)), "set_precision")
+
+    def set_band_width(self, b: int):
+        self._check(self._lib.elsi_set_band_width(self._h, int(b)), "set_band_width")
+
+    def set_refine_max_iter(self, it: int):
+        self._check(self._lib.elsi_set_refine_max_iter(self._h, int(it)), "set_refine_max_iter")
+
+    def set_reuse_ovlp_factor(self, r: bool):
+        self._check(self._lib.elsi_set_reuse_ovlp_factor(self._h, int(bool(r))), "set_reuse_ovlp_factor")
+
+    def set_stream(self, stream):
+        ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._check(self._lib.elsi_set_stream(self._h, _vp(ptr)), "set_stream")
+
+    def use_current_stream(self):
+        import torch
+        self.set_stream(torch.cuda.current_stream())
+
+    # -- solves
+    def ev_real(self, ham, ovlp=None):
+        """Returns (eval (n,), evec (n, n_state)) as CUDA tensors."""
+        import torch
+        ev = torch.empty(self.n, dtype=torch.float64, device=ham.device)
+        vec = torch.empty((self.n_state, self.n), dtype=torch.float64, device=ham.device)
+        rc = self._lib.elsi_ev_real(self._h, _vp(_ptr(ham)), _vp(_ptr(ovlp) if ovlp is not None else None),
+                                    _vp(_ptr(ev)), _vp(_ptr(vec)))
+        self._check(rc, "elsi_ev_real")
+        return ev, vec.t()
+
+    def dm_real(self, ham, ovlp=None, out=None):
+        """Returns (P (n, n), band energy) ; W is kept for get_edm()."""
+        import torch
+        p = out if out is not None else torch.empty((self.n, self.n), dtype=torch.float64, device=ham.device)
+        e = ctypes.c_double(0.0)
+        rc = self._lib.elsi_dm_real(self._h, _vp(_ptr(ham)), _vp(_ptr(ovlp) if ovlp is not None else None),
+                                    _vp(_ptr(p)), ctypes.byref(e))
+        self._check(rc, "elsi_dm_real")
+        return p, e.value
+
+    def get_edm(self, out=None):
+        import torch
+        w = out if out is not None else torch.empty((self.n, self.n), dtype=torch.float64, device="cuda")
+        self._check(self._lib.elsi_get_edm_real(self._h, _vp(_ptr(w))), "elsi_get_edm_real")
+        return w
+
+    def get_mu(self) -> float:
+        mu = ctypes.c_double(0.0)
+        self._check(self._lib.elsi_get_mu(self._h, ctypes.byref(mu)), "elsi_get_mu")
+        return mu.value
+
+    def get_occ(self):
+        import torch
+        f = torch.empty(self.n_state, dtype=torch.float64, device="cuda")
+        self._check(self._lib.elsi_get_occ(self._h, _vp(_ptr(f))), "elsi_get_occ")
+        return f
+
+    def dm_real_host(self, ham, ovlp, den, edm=None) -> float:
+        """Host-buffer entry point: numpy or pinned torch CPU float64 arrays (n, n)."""
+        def hp(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                return a.data_ptr()
+            return a.ctypes.data
+        e = ctypes.c_double(0.0)
+        rc = self._lib.elsi_dm_real_host(self._h, _vp(hp(ham)), _vp(hp(ovlp)), _vp(hp(den)),
+                                         _vp(hp(edm)), ctypes.byref(e))
+        self._check(rc, "elsi_dm_real_host")
+        return e.value
+
+    def stage_times(self) -> dict:
+        buf = (ctypes.c_float * 32)()
+        m = self._lib.elsi_get_stage_times(self._h, buf, 32)
+        return {self._lib.elsi_stage_name(i).decode(): float(buf[i]) for i in range(max(m, 0))}
+
+    def refine_info(self):
+        it, err = ctypes.c_int(0), ctypes.c_double(0.0)
+        self._lib.elsi_get_refine_info(self._h, ctypes.byref(it), ctypes.byref(err))
+        return it.value, err.value
+
+
+def solve_dm(ham, ovlp, n_state: int, n_electron: float, **opts):
+    """One-shot density-matrix solve. Returns dict(P, W, energy, mu)."""
+    with Handle(ham.shape[0], n_state, n_electron) as h:
+        _apply_opts(h, opts)
+        p, e = h.dm_real(ham, ovlp)
+        return dict(P=p, W=h.get_edm(), energy=e, mu=h.get_mu(), stages=h.stage_times())
+
+
+def solve_ev(ham, ovlp, n_state: int, **opts):
+    with Handle(ham.shape[0], n_state, 0.0) as h:
+        _apply_opts(h, opts)
+        ev, vec = h.ev_real(ham, ovlp)
+        return dict(eval=ev, C=vec, stages=h.stage_times())
+
+
+def _apply_opts(h: Handle, opts: dict):
+    if opts.get("overlap_is_unit"):
+        h.set_overlap_is_unit(True)
+    if "band_width" in opts:
+        h.set_band_width(opts["band_width"])
+    if "precision" in opts:
+        h.set_precision(opts["precision"])
+    if "scheme" in opts:
+        h.set_broadening(opts["scheme"], opts.get("kt"))
+    if "occ_accuracy" in opts:
+        h.set_occ_accuracy(opts["occ_accuracy"])
+    if "mu_max_steps" in opts:
+        h.set_mu_max_steps(opts["mu_max_steps"])
+    if "refine_max_iter" in opts:
+        h.set_refine_max_iter(opts["refine_max_iter"])
+    if opts.get("use_current_stream", True):
+        h.use_current_stream()

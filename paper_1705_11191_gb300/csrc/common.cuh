@@ -1,0 +1,90 @@
+// Shared helpers for the GB300 (sm_103a) dense Kohn-Sham solver kernels.
+// Storage convention everywhere: column-major, element (i, j) of a matrix with leading
+// dimension ld at a[i + j * ld].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "elsi_gb.h"
+
+namespace egb {
+
+// Device status word layout (one int array per handle, zeroed before each call):
+//   [0] first error code seen by any kernel (ELSI_ERR_*), 0 = none
+//   [1] auxiliary value (e.g. failing Cholesky pivot, 0-based)
+enum { ST_CODE = 0, ST_AUX = 1, ST_WORDS = 8 };
+
+__device__ __forceinline__ void report_error(int *status, int code, int aux)
+{
+    if (atomicCAS(status + ST_CODE, 0, code) == 0) status[ST_AUX] = aux;
+}
+
+// Iteration limit for every spin wait in this library. With a 64 ns back-off this is
+// several seconds, far longer than any legitimate wait; on expiry the waiting kernel
+// records ELSI_ERR_TIMEOUT and returns.
+constexpr long long kSpinLimit = 1ll << 26;
+
+// Grid-wide barrier for cooperative launches (all CTAs co-resident by construction).
+// count/gen live in global memory and are zero before the launch. Returns false if the
+// wait timed out or another CTA reported an error; the caller must then return.
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen,
+                                             unsigned nblocks, int *status)
+{
+    __shared__ int ok_flag;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *vgen = gen;
+        unsigned my_gen = *vgen;
+        __threadfence();
+        unsigned arrived = atomicAdd(count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long it = 0;
+            volatile int *vst = status;
+            while (*vgen == my_gen) {
+                if (vst[ST_CODE] != 0) { ok = 0; break; }
+                if (++it > kSpinLimit) { report_error(status, ELSI_ERR_TIMEOUT, 0); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_flag = ok;
+    }
+    __syncthreads();
+    return ok_flag != 0;
+}
+
+template <typename T> __device__ __forceinline__ T dsqrt(T x);
+template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+
+// Block-wide sum of one value per thread (blockDim.x multiple of 32, <= 1024).
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *red /* >= 32 entries of shared */)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    T s = (lane < nw) ? red[lane] : T(0);
+    if (warp == 0) {
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[0] = s;
+    }
+    __syncthreads();
+    T r = red[0];
+    __syncthreads();
+    return r;
+}
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace egb

@@ -1,0 +1,287 @@
+// C ABI of the solver (declared in include/elsi_gb.h): handle management, customisation,
+// workspace, and the stage sequence of one solve (arXiv:1705.11191 sec. 3.1 steps and
+// sec. 4.3-4.6 interface).
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <utility>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "solver.h"
+
+using namespace egb;
+
+namespace egb {
+
+const char *const kStageNames[kNumStages] = {
+    "cholesky",  "standard_form", "full_to_band", "band_to_tri", "tridiag_solve",
+    "back_q2",   "back_q1",       "back_subst",   "refine",      "occupation",
+    "density",
+};
+
+int set_error(elsi_gb_handle_s *h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->last_error = buf;
+    return code;
+}
+
+bool ensure_buf(void **p, size_t *cap, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (*p && *cap >= bytes) return true;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, bytes) != cudaSuccess) { *p = nullptr; return false; }
+    *cap = bytes;
+    return true;
+}
+
+}  // namespace egb
+
+static int check_handle(elsi_handle h)
+{
+    if (!h || h->magic != kHandleMagic) return ELSI_ERR_STATE;
+    return ELSI_OK;
+}
+
+extern "C" {
+
+const char *elsi_gb_version(void) { return "elsi-gb300 0.1"; }
+
+int elsi_init(elsi_handle *out, int solver, int fmt, int mode, int n_basis, int n_state,
+              double n_electron)
+{
+    if (!out) return ELSI_ERR_ARG;
+    *out = nullptr;
+    if (solver != ELSI_SOLVER_ELPA) return ELSI_ERR_UNSUPPORTED;
+    if (fmt != ELSI_FORMAT_DENSE) return ELSI_ERR_UNSUPPORTED;
+    if (mode != ELSI_MODE_MULTI_PROC && mode != ELSI_MODE_SINGLE_PROC) return ELSI_ERR_ARG;
+    if (n_basis < 1 || n_state < 1 || n_state > n_basis) return ELSI_ERR_ARG;
+    if (!(n_electron >= 0.0) || n_electron > 2.0 * n_state) return ELSI_ERR_ARG;
+    elsi_gb_handle_s *h = new (std::nothrow) elsi_gb_handle_s();
+    if (!h) return ELSI_ERR_NOMEM;
+    h->magic = kHandleMagic;
+    h->n = n_basis;
+    h->n_state = n_state;
+    h->n_electron = n_electron;
+    *out = h;
+    return ELSI_OK;
+}
+
+int elsi_finalize(elsi_handle *hp)
+{
+    if (!hp || check_handle(*hp)) return ELSI_ERR_STATE;
+    elsi_gb_handle_s *h = *hp;
+    free_workspace(h);
+    h->magic = 0;
+    delete h;
+    *hp = nullptr;
+    return ELSI_OK;
+}
+
+int elsi_set_overlap_is_unit(elsi_handle h, int v)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    h->overlap_is_unit = v != 0;
+    h->have_l = false;
+    return ELSI_OK;
+}
+
+int elsi_set_broadening_scheme(elsi_handle h, int s)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (s == 3 || s == 4)
+        return set_error(h, ELSI_ERR_UNSUPPORTED, "Methfessel-Paxton broadening is not provided");
+    if (s < 0 || s > 2) return set_error(h, ELSI_ERR_ARG, "broadening scheme %d", s);
+    h->scheme = s;
+    return ELSI_OK;
+}
+
+int elsi_set_broadening_width(elsi_handle h, double w)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!(w > 0.0)) return set_error(h, ELSI_ERR_ARG, "broadening width must be > 0");
+    h->kt = w;
+    return ELSI_OK;
+}
+
+int elsi_set_occ_accuracy(elsi_handle h, double a)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!(a > 0.0)) return set_error(h, ELSI_ERR_ARG, "occ_accuracy must be > 0");
+    h->occ_accuracy = a;
+    return ELSI_OK;
+}
+
+int elsi_set_mu_max_steps(elsi_handle h, int s)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (s < 0) return set_error(h, ELSI_ERR_ARG, "mu_max_steps must be >= 0");
+    h->mu_max_steps = s;
+    return ELSI_OK;
+}
+
+int elsi_set_precision(elsi_handle h, int p)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (p != ELSI_PREC_FP64 && p != ELSI_PREC_FP32_REFINE)
+        return set_error(h, ELSI_ERR_ARG, "precision %d", p);
+    h->precision = p;
+    return ELSI_OK;
+}
+
+int elsi_set_band_width(elsi_handle h, int b)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (b < 8 || b > 64 || (b % 8)) return set_error(h, ELSI_ERR_ARG, "band width %d", b);
+    h->band_width = b;
+    return ELSI_OK;
+}
+
+int elsi_set_refine_max_iter(elsi_handle h, int it)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (it < 0 || it > 8) return set_error(h, ELSI_ERR_ARG, "refine iterations %d", it);
+    h->refine_max_iter = it;
+    return ELSI_OK;
+}
+
+int elsi_set_stream(elsi_handle h, void *s)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    h->stream = (cudaStream_t)s;
+    return ELSI_OK;
+}
+
+int elsi_set_reuse_ovlp_factor(elsi_handle h, int r)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    h->reuse_l = r != 0;
+    return ELSI_OK;
+}
+
+int elsi_ev_real(elsi_handle h, double *ham, const double *ovlp, double *eval, double *evec)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!ham || !eval || !evec || (!ovlp && !h->overlap_is_unit))
+        return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    SolveRequest rq;
+    rq.ham = ham; rq.ovlp = ovlp; rq.eval = eval; rq.evec = evec;
+    return run_solve(h, rq);
+}
+
+int elsi_dm_real(elsi_handle h, double *ham, const double *ovlp, double *den_mat, double *energy)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!ham || !den_mat || (!ovlp && !h->overlap_is_unit))
+        return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    SolveRequest rq;
+    rq.ham = ham; rq.ovlp = ovlp; rq.dm = den_mat; rq.want_edm = true;
+    int rc = run_solve(h, rq);
+    if (rc == ELSI_OK && energy) *energy = h->energy;
+    return rc;
+}
+
+int elsi_get_edm_real(elsi_handle h, double *edm)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!edm) return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    if (!h->have_edm) return set_error(h, ELSI_ERR_STATE, "no density-matrix solve yet");
+    size_t bytes = sizeof(double) * (size_t)h->n * h->n;
+    if (cudaMemcpyAsync(edm, h->wk.edm, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return set_error(h, ELSI_ERR_CUDA, "copy of W failed");
+    return ELSI_OK;
+}
+
+int elsi_get_mu(elsi_handle h, double *mu)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!mu) return ELSI_ERR_ARG;
+    if (!h->have_occ) return set_error(h, ELSI_ERR_STATE, "no density-matrix solve yet");
+    *mu = h->mu;
+    return ELSI_OK;
+}
+
+int elsi_get_occ(elsi_handle h, double *occ)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!occ) return ELSI_ERR_ARG;
+    if (!h->have_occ) return set_error(h, ELSI_ERR_STATE, "no density-matrix solve yet");
+    if (cudaMemcpyAsync(occ, h->wk.f, sizeof(double) * h->n_state, cudaMemcpyDeviceToDevice,
+                        h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return set_error(h, ELSI_ERR_CUDA, "copy of occupations failed");
+    return ELSI_OK;
+}
+
+int elsi_dm_real_host(elsi_handle h, const double *ham_host, const double *ovlp_host,
+                      double *den_host, double *edm_host, double *energy)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!ham_host || !den_host || (!ovlp_host && !h->overlap_is_unit))
+        return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    const size_t bytes = sizeof(double) * (size_t)h->n * h->n;
+    if (!ensure_buf((void **)&h->wk.host_h, &h->wk.host_h_cap, bytes) ||
+        !ensure_buf((void **)&h->wk.host_s, &h->wk.host_s_cap, bytes) ||
+        !ensure_buf((void **)&h->wk.host_p, &h->wk.host_p_cap, bytes))
+        return set_error(h, ELSI_ERR_NOMEM, "staging buffers");
+    cudaStream_t st = h->stream;
+    if (cudaMemcpyAsync(h->wk.host_h, ham_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return set_error(h, ELSI_ERR_CUDA, "H2D copy of ham");
+    if (ovlp_host && !(h->reuse_l && h->have_l) &&
+        cudaMemcpyAsync(h->wk.host_s, ovlp_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return set_error(h, ELSI_ERR_CUDA, "H2D copy of ovlp");
+    SolveRequest rq;
+    rq.ham = h->wk.host_h; rq.ovlp = ovlp_host ? h->wk.host_s : nullptr;
+    rq.dm = h->wk.host_p; rq.want_edm = true;
+    int rc = run_solve(h, rq);
+    if (rc != ELSI_OK) return rc;
+    if (cudaMemcpyAsync(den_host, h->wk.host_p, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return set_error(h, ELSI_ERR_CUDA, "D2H copy of P");
+    if (edm_host && cudaMemcpyAsync(edm_host, h->wk.edm, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return set_error(h, ELSI_ERR_CUDA, "D2H copy of W");
+    if (cudaStreamSynchronize(st) != cudaSuccess) return set_error(h, ELSI_ERR_CUDA, "sync");
+    if (energy) *energy = h->energy;
+    return ELSI_OK;
+}
+
+int elsi_get_stage_times(elsi_handle h, float *ms, int n)
+{
+    if (check_handle(h)) return -1;
+    if (!ms) return 0;
+    int m = n < kNumStages ? n : kNumStages;
+    for (int i = 0; i < m; ++i) ms[i] = h->stage_ms[i];
+    return m;
+}
+
+const char *elsi_stage_name(int i)
+{
+    if (i < 0 || i >= kNumStages) return "";
+    return kStageNames[i];
+}
+
+int elsi_get_refine_info(elsi_handle h, int *iters, double *orth_err)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (iters) *iters = h->refine_iters;
+    if (orth_err) *orth_err = h->orth_err;
+    return ELSI_OK;
+}
+
+const char *elsi_get_last_error(elsi_handle h)
+{
+    if (check_handle(h)) return "invalid handle";
+    return h->last_error.c_str();
+}
+
+}  // extern "C"

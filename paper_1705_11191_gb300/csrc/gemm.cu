@@ -1,0 +1,258 @@
+// Register-tiled SIMT GEMM and small matrix utilities.
+//
+// The binary64 path of this solver is bound by the FP64 FMA rate of the chip, which
+// any register-tiled kernel saturates, so the GEMM here is a plain shared-memory tiled
+// kernel: each CTA computes a BM x BN tile of C, staging BK-deep slices of op(A) and
+// op(B) in shared memory, each thread accumulating a TM x TN block in registers.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace egb {
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+gemm_kernel(int m, int n, int k, T alpha, const T *__restrict__ A, int lda, int ta,
+            const T *__restrict__ B, int ldb, int tb, T beta, T *__restrict__ C, int ldc,
+            int uplo)
+{
+    constexpr int NT = (BM / TM) * (BN / TN);
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+
+    const int m0 = blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    if (uplo == 1 && m0 + BM - 1 < n0) return;  // tile entirely above the diagonal
+
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN);  // column group
+    const int ty = tid / (BN / TN);  // row group
+
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+    for (int k0 = 0; k0 < k; k0 += BK) {
+        // ---- stage op(A)[m0:m0+BM, k0:k0+BK] as As[kk][i]
+#pragma unroll
+        for (int r = 0; r < (BM * BK + NT - 1) / NT; ++r) {
+            int e = tid + r * NT;
+            if (e < BM * BK) {
+                int i, kk;
+                if (ta == 0) { i = e % BM; kk = e / BM; } else { kk = e % BK; i = e / BK; }
+                int gi = m0 + i, gk = k0 + kk;
+                T v = T(0);
+                if (gi < m && gk < k)
+                    v = (ta == 0) ? A[(size_t)gi + (size_t)gk * lda] : A[(size_t)gk + (size_t)gi * lda];
+                As[kk][i] = v;
+            }
+        }
+        // ---- stage op(B)[k0:k0+BK, n0:n0+BN] as Bs[kk][j]
+#pragma unroll
+        for (int r = 0; r < (BN * BK + NT - 1) / NT; ++r) {
+            int e = tid + r * NT;
+            if (e < BN * BK) {
+                int j, kk;
+                if (tb == 0) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
+                int gj = n0 + j, gk = k0 + kk;
+                T v = T(0);
+                if (gj < n && gk < k)
+                    v = (tb == 0) ? B[(size_t)gk + (size_t)gj * ldb] : B[(size_t)gj + (size_t)gk * ldb];
+                Bs[kk][j] = v;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], bb[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * (BM / TM)];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + j * (BN / TN)];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        int gi = m0 + ty + i * (BM / TM);
+        if (gi >= m) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            int gj = n0 + tx + j * (BN / TN);
+            if (gj >= n) continue;
+            if (uplo == 1 && gi < gj) continue;
+            T *c = C + (size_t)gi + (size_t)gj * ldc;
+            T v = alpha * acc[i][j];
+            if (beta != T(0)) v = fma(beta, *c, v);
+            *c = v;
+        }
+    }
+}
+
+template <typename T> struct GemmCfg;
+template <> struct GemmCfg<double> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
+template <> struct GemmCfg<float> { static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8; };
+
+template <typename T>
+cudaError_t gemm(cudaStream_t st, int ta, int tb, int m, int n, int k, T alpha, const T *A,
+                 int lda, const T *B, int ldb, T beta, T *C, int ldc, int uplo)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    using G = GemmCfg<T>;
+    dim3 grid(ceil_div(m, G::BM), ceil_div(n, G::BN));
+    dim3 block((G::BM / G::TM) * (G::BN / G::TN));
+    gemm_kernel<T, G::BM, G::BN, G::BK, G::TM, G::TN><<<grid, block, 0, st>>>(
+        m, n, k, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, uplo);
+    return cudaGetLastError();
+}
+
+template cudaError_t gemm<double>(cudaStream_t, int, int, int, int, int, double, const double *,
+                                  int, const double *, int, double, double *, int, int);
+template cudaError_t gemm<float>(cudaStream_t, int, int, int, int, int, float, const float *,
+                                 int, const float *, int, float, float *, int, int);
+
+// ------------------------------------------------------------------ utilities
+template <typename Td, typename Ts>
+__global__ void copy_matrix_kernel(int m, int n, const Ts *__restrict__ src, int lds,
+                                   Td *__restrict__ dst, int ldd)
+{
+    size_t total = (size_t)m * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e % m), j = (int)(e / m);
+        dst[(size_t)i + (size_t)j * ldd] = (Td)src[(size_t)i + (size_t)j * lds];
+    }
+}
+
+template <typename Td, typename Ts>
+cudaError_t copy_matrix(cudaStream_t st, int m, int n, const Ts *src, int lds, Td *dst, int ldd)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    size_t total = (size_t)m * n;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 32) grid = 152 * 32;
+    copy_matrix_kernel<Td, Ts><<<grid, 256, 0, st>>>(m, n, src, lds, dst, ldd);
+    return cudaGetLastError();
+}
+template cudaError_t copy_matrix<double, double>(cudaStream_t, int, int, const double *, int, double *, int);
+template cudaError_t copy_matrix<float, double>(cudaStream_t, int, int, const double *, int, float *, int);
+template cudaError_t copy_matrix<double, float>(cudaStream_t, int, int, const float *, int, double *, int);
+template cudaError_t copy_matrix<float, float>(cudaStream_t, int, int, const float *, int, float *, int);
+
+// 32x32 tiles; mode 0: dst = src^T (general), mode 1: upper := lower^T, mode 2: (a+a^T)/2
+template <typename T>
+__global__ void tile_transpose_kernel(int m, int n, const T *src, int lds, T *dst, int ldd,
+                                      int mode)
+{
+    __shared__ T tile[32][33];
+    int bi = blockIdx.x * 32, bj = blockIdx.y * 32;  // tile of src rows bi.., cols bj..
+    if (mode != 0 && bi < bj) return;                  // symmetric modes: lower tiles only
+    int tx = threadIdx.x, ty = threadIdx.y;            // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        int i = bi + tx, j = bj + r;
+        if (i < m && j < n) tile[r][tx] = src[(size_t)i + (size_t)j * lds];
+    }
+    __syncthreads();
+    if (mode == 2) {
+        // average tile (bi,bj) with tile (bj,bi) and write both
+        __shared__ T tile2[32][33];
+        for (int r = ty; r < 32; r += 8) {
+            int i = bj + tx, j = bi + r;
+            if (i < n && j < m) tile2[r][tx] = src[(size_t)i + (size_t)j * lds];
+        }
+        __syncthreads();
+        // tile[r][c] = a(bi+c, bj+r); tile2[r][c] = a(bj+c, bi+r)
+        for (int r = ty; r < 32; r += 8) {
+            int i = bi + tx, j = bj + r;
+            if (i < m && j < n) {
+                T v = T(0.5) * (tile[r][tx] + tile2[tx][r]);
+                dst[(size_t)i + (size_t)j * ldd] = v;
+            }
+        }
+        for (int r = ty; r < 32; r += 8) {
+            int i = bj + tx, j = bi + r;
+            if (i < n && j < m) {
+                T v = T(0.5) * (tile2[r][tx] + tile[tx][r]);
+                dst[(size_t)i + (size_t)j * ldd] = v;
+            }
+        }
+        return;
+    }
+    // write transposed: dst(j, i) = src(i, j)
+    for (int r = ty; r < 32; r += 8) {
+        int j = bj + tx, i = bi + r;  // dst row j = src col, dst col i = src row
+        if (i < m && j < n) {
+            if (mode == 1 && i <= j) continue;  // only strictly-lower sources to upper
+            dst[(size_t)j + (size_t)i * ldd] = tile[tx][r];
+        }
+    }
+}
+
+template <typename T>
+cudaError_t transpose(cudaStream_t st, int m, int n, const T *src, int lds, T *dst, int ldd)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    dim3 grid(ceil_div(m, 32), ceil_div(n, 32)), block(32, 8);
+    tile_transpose_kernel<T><<<grid, block, 0, st>>>(m, n, src, lds, dst, ldd, 0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mirror_lower(cudaStream_t st, int n, T *a, int lda)
+{
+    if (n <= 0) return cudaSuccess;
+    dim3 grid(ceil_div(n, 32), ceil_div(n, 32)), block(32, 8);
+    tile_transpose_kernel<T><<<grid, block, 0, st>>>(n, n, a, lda, a, lda, 1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t symmetrize(cudaStream_t st, int n, T *a, int lda)
+{
+    if (n <= 0) return cudaSuccess;
+    dim3 grid(ceil_div(n, 32), ceil_div(n, 32)), block(32, 8);
+    tile_transpose_kernel<T><<<grid, block, 0, st>>>(n, n, a, lda, a, lda, 2);
+    return cudaGetLastError();
+}
+
+template cudaError_t transpose<double>(cudaStream_t, int, int, const double *, int, double *, int);
+template cudaError_t transpose<float>(cudaStream_t, int, int, const float *, int, float *, int);
+template cudaError_t mirror_lower<double>(cudaStream_t, int, double *, int);
+template cudaError_t mirror_lower<float>(cudaStream_t, int, float *, int);
+template cudaError_t symmetrize<double>(cudaStream_t, int, double *, int);
+template cudaError_t symmetrize<float>(cudaStream_t, int, float *, int);
+
+template <typename T>
+__global__ void check_finite_kernel(int m, int n, const T *a, int lda, int *status)
+{
+    size_t total = (size_t)m * n;
+    bool bad = false;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e % m), j = (int)(e / m);
+        T v = a[(size_t)i + (size_t)j * lda];
+        if (!isfinite(v)) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+        report_error(status, ELSI_ERR_NONFINITE, 0);
+}
+
+template <typename T>
+cudaError_t check_finite(cudaStream_t st, int m, int n, const T *a, int lda, int *status)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    size_t total = (size_t)m * n;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    check_finite_kernel<T><<<grid, 256, 0, st>>>(m, n, a, lda, status);
+    return cudaGetLastError();
+}
+template cudaError_t check_finite<double>(cudaStream_t, int, int, const double *, int, int *);
+template cudaError_t check_finite<float>(cudaStream_t, int, int, const float *, int, int *);
+
+}  // namespace egb

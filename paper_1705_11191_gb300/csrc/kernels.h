@@ -1,0 +1,97 @@
+// Internal launchers of the solver kernels (not part of the C ABI).
+// All matrices are column-major; every launcher enqueues on `st` and returns the launch
+// status (cudaSuccess or the error of the launch).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace egb {
+
+// C = alpha * op(A) * op(B) + beta * C, op(A) m x k, op(B) k x n. ta/tb: 0 = N, 1 = T.
+// uplo = 1: only the lower triangle (row >= col) of C is computed and written.
+// beta == 0 means C is not read.
+template <typename T>
+cudaError_t gemm(cudaStream_t st, int ta, int tb, int m, int n, int k, T alpha,
+                 const T *A, int lda, const T *B, int ldb, T beta, T *C, int ldc,
+                 int uplo = 0);
+
+// dst(m x n, ldd) = src(m x n, lds), with type conversion.
+template <typename Td, typename Ts>
+cudaError_t copy_matrix(cudaStream_t st, int m, int n, const Ts *src, int lds, Td *dst, int ldd);
+
+// a(n x n): upper triangle := transpose of the lower triangle.
+template <typename T>
+cudaError_t mirror_lower(cudaStream_t st, int n, T *a, int lda);
+
+// dst(n x m) = src(m x n)^T
+template <typename T>
+cudaError_t transpose(cudaStream_t st, int m, int n, const T *src, int lds, T *dst, int ldd);
+
+// a := (a + a^T) / 2 for an n x n matrix.
+template <typename T>
+cudaError_t symmetrize(cudaStream_t st, int n, T *a, int lda);
+
+// Sets status ELSI_ERR_NONFINITE if any entry of the m x n matrix is NaN/Inf.
+template <typename T>
+cudaError_t check_finite(cudaStream_t st, int m, int n, const T *a, int lda, int *status);
+
+// ---- Cholesky and triangular solves (Eqs. 8-9) ----
+// Lower Cholesky of the n x n matrix a in place (upper triangle zeroed). inv_diag
+// receives the inverses of the nb x nb diagonal blocks of L (n x nb, block j at rows
+// j*nb). work: n x nb scratch. Status ELSI_ERR_NOT_PD with the pivot on failure.
+template <typename T>
+cudaError_t potrf(cudaStream_t st, int n, T *a, int lda, T *inv_diag, T *work, int *status);
+constexpr int kTriBlock = 64;  // nb of potrf / trsm
+
+// B (n x ncol) := L^{-1} B (trans = 0) or L^{-T} B (trans = 1), L lower from potrf,
+// inv_diag its diagonal-block inverses. work: kTriBlock x ncol scratch.
+template <typename T>
+cudaError_t trsm_left_lower(cudaStream_t st, int trans, int n, int ncol, const T *L, int ldl,
+                            const T *inv_diag, T *B, int ldb, T *work);
+
+// ---- full -> band (Eq. 11, first line) ----
+template <typename T>
+cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T *work,
+                  size_t work_elems, unsigned *sync, int *status, int num_sms);
+size_t sy2sb_work_elems(int n, int b);
+
+// ---- band -> tridiagonal (Eq. 11, second line) ----
+// band: lower band storage with ldb >= 2b+1 (element (r,c), r>=c, at band[(r-c) + c*ldb]).
+// Outputs d (n), e (n-1) as double, reflectors v2 (b per slot) and tau2.
+int sb2st_steps(int n, int b);
+template <typename T>
+cudaError_t sb2st(cudaStream_t st, int n, int b, T *band, int ldb, double *d, double *e,
+                  T *v2, T *tau2, int *status, unsigned *sync, int num_sms);
+template <typename T>
+cudaError_t extract_band(cudaStream_t st, int n, int b, const T *a, int lda, T *band, int ldb);
+
+// ---- tridiagonal eigensolver (sec. 3.1, step 3) ----
+// Eigenvalues il..iu-1 (0-based, ascending) of the symmetric tridiagonal (d, e) by
+// Sturm bisection (w needs count + 4 entries: the Gershgorin bounds follow the values),
+// then eigenvectors of the first kvec of them into z (n x kvec, ldz) as type T.
+// scratch: 2*n*kvec + 8 doubles.
+cudaError_t stebz(cudaStream_t st, int n, const double *d, const double *e, int count,
+                  double *w, int *status);
+template <typename T>
+cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int kvec,
+                  const double *w, T *z, int ldz, double *scratch, int *cluster_ws,
+                  int *status);
+
+// ---- back-transformations (steps 4 and 5) ----
+template <typename T>
+cudaError_t apply_q2(cudaStream_t st, int n, int b, const T *v2, const T *tau2, int k,
+                     T *z, int ldz, int *status);
+template <typename T>
+cudaError_t apply_q1(cudaStream_t st, int n, int b, int k, const T *v1, const T *t1, T *z,
+                     int ldz, T *work);
+
+// ---- occupation, density matrices ----
+cudaError_t occupation(cudaStream_t st, int k, const double *eps, double n_el, int scheme,
+                       double kt, double occ_accuracy, int mu_max_steps, double *f,
+                       double *out /* [0]=mu [1]=energy */, int *status);
+// P = C diag(f) C^T and W = C diag(f eps) C^T (lower + mirror); cw: n x k scratch.
+template <typename T>
+cudaError_t density_pw(cudaStream_t st, int n, int k, const T *c, int ldc, const double *f,
+                       const double *eps, T *p, T *w, T *cw);
+
+}  // namespace egb

@@ -1,0 +1,223 @@
+// Stage sequence of one solve (arXiv:1705.11191 sec. 3.1, Eqs. 8-11 and steps (1)-(5);
+// sec. 4.4 for the occupation and density matrix).
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "solver.h"
+
+namespace egb {
+
+void free_workspace(elsi_gb_handle_s *h)
+{
+    Workspace &w = h->wk;
+    void *bufs[] = {w.a, w.l, w.v1, w.edm, w.v2, w.tau2, w.band, w.t1, w.invd, w.work, w.z,
+                    w.d, w.e, w.w, w.f, w.scal, w.stein, w.rf, w.sync, w.status,
+                    w.host_h, w.host_s, w.host_p};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (w.status_host) cudaFreeHost(w.status_host);
+    if (w.scal_host) cudaFreeHost(w.scal_host);
+    if (w.events_ready)
+        for (auto &e : w.ev) cudaEventDestroy(e);
+    h->wk = Workspace();
+}
+
+#define ENSURE(name, type, count)                                                          \
+    if (!ensure_buf((void **)&w.name, &w.name##_cap, sizeof(type) * (size_t)(count)))     \
+        return set_error(h, ELSI_ERR_NOMEM, "cannot allocate %s (%zu bytes)", #name,       \
+                         sizeof(type) * (size_t)(count));
+
+static int ensure_workspace(elsi_gb_handle_s *h, int kz)
+{
+    Workspace &w = h->wk;
+    const size_t n = h->n;
+    const int b = h->band_width;
+    const int S = sb2st_steps(h->n, b);
+    const size_t nsweep = n >= 3 ? n - 2 : 1;
+    ENSURE(a, double, n * n);
+    ENSURE(l, double, n * n);
+    ENSURE(v1, double, n * n);
+    ENSURE(edm, double, n * n);
+    ENSURE(v2, double, nsweep * S * b);
+    ENSURE(tau2, double, nsweep * S);
+    ENSURE(band, double, (2 * b + 1) * n);
+    ENSURE(t1, double, (size_t)b * n);
+    ENSURE(invd, double, n * kTriBlock);
+    size_t work = n * kTriBlock;
+    size_t wsy = sy2sb_work_elems(h->n, b);
+    if (wsy > work) work = wsy;
+    if ((size_t)2 * b * kz > work) work = (size_t)2 * b * kz;
+    ENSURE(work, double, work + 64);
+    ENSURE(z, double, n * kz);
+    ENSURE(d, double, n + 8);
+    ENSURE(e, double, n + 8);
+    ENSURE(w, double, n + 8);
+    ENSURE(f, double, n + 8);
+    ENSURE(scal, double, 64);
+    ENSURE(stein, double, 2 * n * kz + 16);
+    ENSURE(sync, unsigned, 64 + 2 * (1024 + 64 + 1024 * 64 + 1024 * 64 * 64));
+    ENSURE(status, int, ST_WORDS);
+    if (!w.status_host && cudaMallocHost((void **)&w.status_host, sizeof(int) * ST_WORDS) != cudaSuccess)
+        return set_error(h, ELSI_ERR_NOMEM, "pinned status");
+    if (!w.scal_host && cudaMallocHost((void **)&w.scal_host, sizeof(double) * 64) != cudaSuccess)
+        return set_error(h, ELSI_ERR_NOMEM, "pinned scalars");
+    if (!w.events_ready) {
+        for (auto &e : w.ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return set_error(h, ELSI_ERR_CUDA, "event create");
+        w.events_ready = true;
+    }
+    return ELSI_OK;
+}
+
+#define CK(...)                                                                            \
+    do {                                                                                   \
+        cudaError_t _e = (__VA_ARGS__);                                                    \
+        if (_e != cudaSuccess)                                                             \
+            return set_error(h, ELSI_ERR_CUDA, "%s failed: %s", #__VA_ARGS__,              \
+                             cudaGetErrorString(_e));                                      \
+    } while (0)
+
+static int num_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq);
+
+// FP64 route: every stage in binary64.
+static int solve_fp64(elsi_gb_handle_s *h, const SolveRequest &rq)
+{
+    Workspace &w = h->wk;
+    cudaStream_t st = h->stream;
+    const int n = h->n, k = h->n_state, b = h->band_width;
+    const bool unit = h->overlap_is_unit;
+    const int sms = num_sms();
+    const bool ev_mode = rq.evec != nullptr;
+
+    CK(cudaEventRecord(w.ev[STAGE_CHOL], st));
+    // ---- Eq. 8: S = L L^T (skipped when the factor of the previous call is reused)
+    if (!unit && !(h->reuse_l && h->have_l && h->have_l_prec == ELSI_PREC_FP64)) {
+        CK(check_finite<double>(st, n, n, rq.ovlp, n, w.status));
+        CK(copy_matrix<double, double>(st, n, n, rq.ovlp, n, w.l, n));
+        CK(potrf<double>(st, n, w.l, n, w.invd, w.work, w.status));
+        h->have_l_prec = ELSI_PREC_FP64;
+    }
+    CK(cudaEventRecord(w.ev[STAGE_STDFORM], st));
+    // ---- Eq. 9: H~ = L^{-1} H L^{-T}
+    CK(check_finite<double>(st, n, n, rq.ham, n, w.status));
+    double *A = w.a;
+    if (!unit) {
+        CK(copy_matrix<double, double>(st, n, n, rq.ham, n, w.edm, n));
+        CK(trsm_left_lower<double>(st, 0, n, n, w.l, n, w.invd, w.edm, n, w.work));  // Y = L^{-1} H
+        CK(transpose<double>(st, n, n, w.edm, n, A, n));                             // Y^T
+        CK(trsm_left_lower<double>(st, 0, n, n, w.l, n, w.invd, A, n, w.work));      // L^{-1} Y^T
+        CK(symmetrize<double>(st, n, A, n));
+    } else {
+        CK(copy_matrix<double, double>(st, n, n, rq.ham, n, A, n));
+        CK(symmetrize<double>(st, n, A, n));
+    }
+    CK(cudaEventRecord(w.ev[STAGE_SY2SB], st));
+    // ---- Eq. 11 (1): full -> band
+    CK(sy2sb<double>(st, n, b, A, n, w.v1, w.t1, w.work, w.work_cap / sizeof(double), w.sync,
+                     w.status, sms));
+    CK(cudaEventRecord(w.ev[STAGE_SB2ST], st));
+    // ---- Eq. 11 (2): band -> tridiagonal
+    const int ldb = 2 * b + 1;
+    CK(extract_band<double>(st, n, b, A, n, w.band, ldb));
+    CK(sb2st<double>(st, n, b, w.band, ldb, w.d, w.e, w.v2, w.tau2, w.status, w.sync, sms));
+    CK(cudaEventRecord(w.ev[STAGE_TRIDIAG], st));
+    // ---- step (3): eigenvalues (all n for ev, the n_state lowest for dm), k vectors
+    const int nval = ev_mode ? n : k;
+    CK(stebz(st, n, w.d, w.e, nval, w.w, w.status));
+    CK(stein<double>(st, n, w.d, w.e, k, w.w, w.z, n, w.stein, nullptr, w.status));
+    CK(cudaEventRecord(w.ev[STAGE_Q2], st));
+    // ---- step (4): Z <- Q2 Z
+    CK(apply_q2<double>(st, n, b, w.v2, w.tau2, k, w.z, n, w.status));
+    CK(cudaEventRecord(w.ev[STAGE_Q1], st));
+    // ---- step (5): Z <- Q1 Z
+    CK(apply_q1<double>(st, n, b, k, w.v1, w.t1, w.z, n, w.work));
+    CK(cudaEventRecord(w.ev[STAGE_BACKSUB], st));
+    // ---- Eq. 9: c = L^{-T} c~
+    if (!unit) CK(trsm_left_lower<double>(st, 1, n, k, w.l, n, w.invd, w.z, n, w.work));
+    CK(cudaEventRecord(w.ev[STAGE_REFINE], st));
+    CK(cudaEventRecord(w.ev[STAGE_OCC], st));
+    if (ev_mode) {
+        CK(cudaMemcpyAsync(rq.eval, w.w, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(rq.evec, w.z, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, st));
+        CK(cudaEventRecord(w.ev[STAGE_DENSITY], st));
+    } else {
+        // ---- sec. 4.4: mu, occupations, band energy
+        CK(occupation(st, k, w.w, h->n_electron, h->scheme, h->kt, h->occ_accuracy, h->mu_max_steps,
+                      w.f, w.scal, w.status));
+        CK(cudaEventRecord(w.ev[STAGE_DENSITY], st));
+        // ---- Eq. 7: P and W (only columns with possibly nonzero f)
+        int kocc = k;
+        if (h->scheme == ELSI_OCC_INTEGER) {
+            kocc = (int)((h->n_electron + 1.999999999) / 2.0);
+            if (kocc > k) kocc = k;
+            if (kocc < 1) kocc = 1;
+        }
+        CK(density_pw<double>(st, n, kocc, w.z, n, w.f, w.w, rq.dm, rq.want_edm ? w.edm : nullptr, w.v1));
+    }
+    CK(cudaEventRecord(w.ev[kNumStages], st));
+    return ELSI_OK;
+}
+
+int run_solve(elsi_gb_handle_s *h, const SolveRequest &rq)
+{
+    h->last_error.clear();
+    const bool ev_mode = rq.evec != nullptr;
+    int kz = h->n_state;
+    if (h->precision == ELSI_PREC_FP32_REFINE) kz = h->n;
+    int rc = ensure_workspace(h, kz);
+    if (rc) return rc;
+    Workspace &w = h->wk;
+    cudaStream_t st = h->stream;
+    CK(cudaMemsetAsync(w.status, 0, sizeof(int) * ST_WORDS, st));
+    if (h->precision == ELSI_PREC_FP64) rc = solve_fp64(h, rq);
+    else rc = solve_fp32_refine(h, rq);
+    if (rc) {
+        cudaStreamSynchronize(st);
+        return rc;
+    }
+    CK(cudaMemcpyAsync(w.status_host, w.status, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(w.scal_host, w.scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < kNumStages; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, w.ev[i], w.ev[i + 1]) != cudaSuccess) ms = 0.f;
+        h->stage_ms[i] = ms;
+    }
+    const int code = w.status_host[ST_CODE];
+    if (code != 0) {
+        h->have_edm = false;
+        h->have_occ = false;
+        if (code == ELSI_ERR_NOT_PD) {
+            h->have_l = false;
+            return set_error(h, code, "overlap matrix not positive definite (pivot %d)",
+                             w.status_host[ST_AUX]);
+        }
+        if (code == ELSI_ERR_NONFINITE) return set_error(h, code, "non-finite value in the input");
+        if (code == ELSI_ERR_TIMEOUT) return set_error(h, code, "device wait limit reached");
+        if (code == ELSI_ERR_NO_CONVERGENCE)
+            return set_error(h, code, "no convergence (index %d)", w.status_host[ST_AUX]);
+        return set_error(h, code, "device error %d", code);
+    }
+    if (!h->overlap_is_unit) h->have_l = true;
+    if (!ev_mode) {
+        h->mu = w.scal_host[0];
+        h->energy = w.scal_host[1];
+        h->have_occ = true;
+        h->have_edm = rq.want_edm;
+    } else {
+        h->have_edm = false;
+    }
+    return ELSI_OK;
+}
+
+}  // namespace egb

@@ -1,0 +1,99 @@
+// Handle and workspace of one solver instance (the elsi_handle of arXiv:1705.11191
+// sec. 4.1: all runtime parameters live in the handle, no globals).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <string>
+
+#include "elsi_gb.h"
+
+namespace egb {
+
+constexpr unsigned kHandleMagic = 0xE151C0DEu;
+enum {
+    STAGE_CHOL = 0, STAGE_STDFORM, STAGE_SY2SB, STAGE_SB2ST, STAGE_TRIDIAG, STAGE_Q2,
+    STAGE_Q1, STAGE_BACKSUB, STAGE_REFINE, STAGE_OCC, STAGE_DENSITY, kNumStages
+};
+extern const char *const kStageNames[kNumStages];
+
+// Device buffers, grown on demand and kept across calls.
+struct Workspace {
+#define EGB_BUF(type, name) type *name = nullptr; size_t name##_cap = 0;
+    EGB_BUF(double, a)       // n x n: H~, then the full -> band reduction in place
+    EGB_BUF(double, l)       // n x n: Cholesky factor (kept for reuse)
+    EGB_BUF(double, v1)      // n x n: explicit panel reflectors of stage 1
+    EGB_BUF(double, edm)     // n x n: W of the last dm call / scratch during a solve
+    EGB_BUF(double, v2)      // stage-2 reflectors
+    EGB_BUF(double, tau2)
+    EGB_BUF(double, band)    // (2b+1) x n
+    EGB_BUF(double, t1)      // b x n
+    EGB_BUF(double, invd)    // n x nb inverses of the diagonal blocks of L
+    EGB_BUF(double, work)
+    EGB_BUF(double, z)       // n x k eigenvectors
+    EGB_BUF(double, d)
+    EGB_BUF(double, e)
+    EGB_BUF(double, w)       // eigenvalues (+ bounds)
+    EGB_BUF(double, f)       // occupations
+    EGB_BUF(double, scal)    // device scalars: mu, energy, refinement diagnostics
+    EGB_BUF(double, stein)   // tridiagonal-eigenvector scratch
+    EGB_BUF(double, rf)      // refinement buffers
+    EGB_BUF(unsigned, sync)  // grid-barrier words + partial sums
+    EGB_BUF(int, status)
+    EGB_BUF(double, host_h)  // staging for the _host entry points
+    EGB_BUF(double, host_s)
+    EGB_BUF(double, host_p)
+#undef EGB_BUF
+    int *status_host = nullptr;  // pinned
+    double *scal_host = nullptr; // pinned
+    cudaEvent_t ev[kNumStages + 1] = {};
+    bool events_ready = false;
+};
+
+}  // namespace egb
+
+struct elsi_gb_handle_s {
+    unsigned magic = 0;
+    int n = 0, n_state = 0;
+    double n_electron = 0.0;
+    // customisation (sec. 4.5) and additions
+    bool overlap_is_unit = false;
+    int scheme = ELSI_OCC_INTEGER;
+    double kt = 0.01;
+    double occ_accuracy = 1e-12;
+    int mu_max_steps = 200;
+    int precision = ELSI_PREC_FP64;
+    int band_width = 64;
+    int refine_max_iter = 3;
+    bool reuse_l = false;
+    cudaStream_t stream = nullptr;
+    // state
+    bool have_l = false;
+    int have_l_prec = -1;
+    bool have_edm = false, have_occ = false;
+    double mu = 0.0, energy = 0.0;
+    int refine_iters = 0;
+    double orth_err = 0.0;
+    float stage_ms[egb::kNumStages] = {};
+    std::string last_error;
+    egb::Workspace wk;
+};
+
+namespace egb {
+
+struct SolveRequest {
+    const double *ham = nullptr;   // device, n x n
+    const double *ovlp = nullptr;  // device, n x n (may be null if overlap_is_unit)
+    double *eval = nullptr;        // ev: n eigenvalues
+    double *evec = nullptr;        // ev: n x n_state
+    double *dm = nullptr;          // dm: P
+    bool want_edm = false;         // dm: keep W in the handle
+};
+
+int set_error(elsi_gb_handle_s *h, int code, const char *fmt, ...);
+bool ensure_buf(void **p, size_t *cap, size_t bytes);
+int run_solve(elsi_gb_handle_s *h, const SolveRequest &rq);
+void free_workspace(elsi_gb_handle_s *h);
+
+}  // namespace egb

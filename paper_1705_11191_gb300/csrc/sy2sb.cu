@@ -1,0 +1,275 @@
+// Full -> band reduction B = Q1^T H~ Q1 (arXiv:1705.11191 Eq. 11, first line; step (1)
+// of the two-stage tridiagonalisation in sec. 3.1).
+//
+// Panel p (columns [p*b, p*b+b), rows [p*b+b, n)) is factorised by blocked Householder
+// QR (compact-WY form Q_p = I - V T V^T); then the trailing symmetric matrix gets the
+// two-sided update A22 <- Q_p^T A22 Q_p = A22 - V W^T - W V^T with
+// X = A22 V T and W = X - (1/2) V (T^T (V^T X)).
+//
+// The panel QR is one cooperative launch: the m x b panel is split by rows over G CTAs,
+// each holding its rows in shared memory; per column there are two grid barriers
+// (norm, then the dot products of the reflector with the remaining columns). The
+// trailing update is GEMM work.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace egb {
+
+struct PanelArgs {
+    int m, bw, rows_per_cta;
+    int lda, ldv;
+    unsigned *count, *gen;  // grid barrier state (zeroed)
+    double *part;            // G partial norms
+    double *alpha;           // [bw] diagonal entries before reflection
+    double *wpart;           // G x bw partial dot products
+    double *gram;            // G x bw x bw partial Gram matrices
+    int *status;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ldt, PanelArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int bw = a.bw, bwp = bw + 1;
+    const int R = a.rows_per_cta;
+    T *Ploc = reinterpret_cast<T *>(smem_raw);          // R x bwp, row-major
+    __shared__ double red[32];
+    __shared__ double tau_s[64];
+    __shared__ double wsum[64];
+    __shared__ double colpart[4][64];
+    const int g = blockIdx.x, G = gridDim.x;
+    const int tid = threadIdx.x;
+    const int row0 = g * R;
+    const int nrow = max(0, min(a.m - row0, R));
+    const int tc = tid & 63, tr = tid >> 6;  // 64 column lanes x 4 row lanes
+
+    for (int e = tid; e < R * bw; e += blockDim.x) {
+        int i = e % R, c = e / R;
+        Ploc[i * bwp + c] = (i < nrow) ? P[(size_t)(row0 + i) + (size_t)c * a.lda] : T(0);
+    }
+    __syncthreads();
+
+    const int nref = min(bw, a.m);
+    for (int j = 0; j < nref; ++j) {
+        // ---- phase A: partial sum of squares below the diagonal of column j
+        double ss = 0.0;
+        for (int i = tid; i < nrow; i += blockDim.x)
+            if (row0 + i > j) { double x = (double)Ploc[i * bwp + j]; ss += x * x; }
+        ss = block_sum(ss, red);
+        if (tid == 0) {
+            a.part[g] = ss;
+            if (j >= row0 && j < row0 + nrow) a.alpha[j] = (double)Ploc[(j - row0) * bwp + j];
+        }
+        if (!grid_barrier(a.count, a.gen, G, a.status)) return;
+        // ---- phase B: reflector of column j (every CTA computes the same numbers)
+        double sigma2 = 0.0;
+        for (int q = 0; q < G; ++q) sigma2 += ((volatile double *)a.part)[q];
+        double alpha = ((volatile double *)a.alpha)[j];
+        double beta, tau, scl;
+        if (sigma2 == 0.0) { beta = alpha; tau = 0.0; scl = 0.0; }
+        else {
+            double nrm = sqrt(alpha * alpha + sigma2);
+            beta = (alpha >= 0.0) ? -nrm : nrm;
+            tau = (beta - alpha) / beta;
+            scl = 1.0 / (alpha - beta);
+        }
+        for (int i = tid; i < nrow; i += blockDim.x)
+            if (row0 + i > j) Ploc[i * bwp + j] = (T)((double)Ploc[i * bwp + j] * scl);
+        __syncthreads();
+        // partial w_c = sum_i v_i P[i][c], c > j, over rows i >= j (v_j = 1)
+        {
+            double s = 0.0;
+            int c = tc;
+            if (c > j && c < bw) {
+                for (int i = tr; i < nrow; i += 4) {
+                    int gi = row0 + i;
+                    if (gi < j) continue;
+                    double v = (gi == j) ? 1.0 : (double)Ploc[i * bwp + j];
+                    s += v * (double)Ploc[i * bwp + c];
+                }
+            }
+            colpart[tr][tc] = s;
+            __syncthreads();
+            if (tid < bw)
+                a.wpart[(size_t)g * bw + tid] =
+                    colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
+        }
+        if (tid == 0) tau_s[j] = tau;
+        if (!grid_barrier(a.count, a.gen, G, a.status)) return;
+        // ---- phase C: apply the reflector to the remaining columns
+        if (tid < bw) {
+            double w = 0.0;
+            if (tid > j)
+                for (int q = 0; q < G; ++q) w += ((volatile double *)a.wpart)[(size_t)q * bw + tid];
+            wsum[tid] = w;
+        }
+        __syncthreads();
+        {
+            int c = tc;
+            if (c > j && c < bw) {
+                double wt = tau * wsum[c];
+                for (int i = tr; i < nrow; i += 4) {
+                    int gi = row0 + i;
+                    if (gi < j) continue;
+                    double v = (gi == j) ? 1.0 : (double)Ploc[i * bwp + j];
+                    Ploc[i * bwp + c] = (T)((double)Ploc[i * bwp + c] - v * wt);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && j >= row0 && j < row0 + nrow) Ploc[(j - row0) * bwp + j] = (T)beta;
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int j = nref; j < bw; ++j) tau_s[j] = 0.0;
+    __syncthreads();
+
+    // ---- write back the panel (R on/above the diagonal, reflector tails below) and the
+    //      explicit V (unit diagonal, zeros above) for the GEMM updates
+    for (int e = tid; e < nrow * bw; e += blockDim.x) {
+        int i = e % nrow, c = e / nrow;
+        int gi = row0 + i;
+        T pv = Ploc[i * bwp + c];
+        P[(size_t)gi + (size_t)c * a.lda] = pv;
+        T vv = (c >= nref) ? T(0) : ((gi > c) ? pv : ((gi == c) ? T(1) : T(0)));
+        V[(size_t)gi + (size_t)c * a.ldv] = vv;
+    }
+    // ---- Gram matrix V^T V (partial per CTA), then T by the forward recurrence
+    for (int e = tid; e < bw * bw; e += blockDim.x) {
+        int r = e % bw, c = e / bw;
+        double s = 0.0;
+        if (r < nref && c < nref && r <= c) {
+            for (int i = 0; i < nrow; ++i) {
+                int gi = row0 + i;
+                double vr = (gi > r) ? (double)Ploc[i * bwp + r] : (gi == r ? 1.0 : 0.0);
+                double vc = (gi > c) ? (double)Ploc[i * bwp + c] : (gi == c ? 1.0 : 0.0);
+                s += vr * vc;
+            }
+        }
+        a.gram[(size_t)g * bw * bw + e] = s;
+    }
+    if (!grid_barrier(a.count, a.gen, G, a.status)) return;
+    if (g != 0) return;
+    double *gsum = reinterpret_cast<double *>(smem_raw);  // reuse: bw x bw (fits: R*bwp*sizeof(T) >= ...)
+    double *tloc = gsum + bw * bw;
+    for (int e = tid; e < bw * bw; e += blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < G; ++q) s += ((volatile double *)a.gram)[(size_t)q * bw * bw + e];
+        gsum[e] = s;
+        tloc[e] = 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < bw; ++j) {
+        // T[0:j, j] = -tau_j * T[0:j, 0:j] * gram[0:j, j]
+        if (tid < j) {
+            double s = 0.0;
+            for (int p = tid; p < j; ++p) s += tloc[tid + p * bw] * gsum[p + j * bw];
+            tloc[tid + j * bw] = -tau_s[j] * s;
+        }
+        if (tid == 0) tloc[j + j * bw] = tau_s[j];
+        __syncthreads();
+    }
+    for (int e = tid; e < bw * bw; e += blockDim.x) {
+        int r = e % bw, c = e / bw;
+        Tm[(size_t)r + (size_t)c * ldt] = (T)tloc[e];
+    }
+}
+
+size_t sy2sb_work_elems(int n, int b)
+{
+    // X (n x b), W (n x b), Y (b x b), Z (b x b)
+    return (size_t)4 * n * b + 4 * (size_t)b * b;
+}
+
+template <typename T>
+cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T *work,
+                  size_t work_elems, unsigned *sync, int *status, int num_sms)
+{
+    cudaError_t e;
+    if (b > 64 || b < 1) return cudaErrorInvalidValue;
+    // sync layout: [0..1] barrier words, then doubles
+    double *dsync = reinterpret_cast<double *>(sync + 64);
+    const int max_g = 1024;
+    double *part = dsync;
+    double *alpha = part + max_g;
+    double *wpart = alpha + 64;
+    double *gram = wpart + (size_t)max_g * 64;
+
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int c0 = 0; c0 + b <= n - 2; c0 += b) {
+        const int r0 = c0 + b;
+        const int m = n - r0;
+        const int bw = b;
+        // rows per CTA: at most 128, and enough CTAs to be co-resident
+        int rows = 128;
+        int G = ceil_div(m, rows);
+        size_t smem = (size_t)rows * (bw + 1) * sizeof(T);
+        size_t smem_t = 2 * (size_t)bw * bw * sizeof(double);
+        if (smem < smem_t) smem = smem_t;
+        static bool attr_set[2] = {false, false};
+        int ai = sizeof(T) == 8 ? 0 : 1;
+        if (!attr_set[ai]) {
+            if ((e = cudaFuncSetAttribute(panel_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          200 * 1024)) != cudaSuccess) return e;
+            attr_set[ai] = true;
+        }
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_qr_kernel<T>, 256, smem);
+        int max_coresident = per_sm * num_sms;
+        while (G > max_coresident || G > max_g) {
+            rows *= 2;
+            G = ceil_div(m, rows);
+            smem = (size_t)rows * (bw + 1) * sizeof(T);
+            if (smem < smem_t) smem = smem_t;
+            if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_qr_kernel<T>, 256, smem);
+            max_coresident = per_sm * num_sms;
+        }
+        if ((e = cudaMemsetAsync(sync, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return e;
+        PanelArgs pa;
+        pa.m = m; pa.bw = bw; pa.rows_per_cta = rows; pa.lda = lda; pa.ldv = n;
+        pa.count = sync; pa.gen = sync + 1;
+        pa.part = part; pa.alpha = alpha; pa.wpart = wpart; pa.gram = gram; pa.status = status;
+        T *P = a + r0 + (size_t)c0 * lda;
+        T *V = v1 + r0 + (size_t)c0 * n;
+        T *Tm = t1 + (size_t)c0 * b;
+        int ldt = b;
+        void *args[] = {&P, &V, &Tm, &ldt, &pa};
+        if ((e = cudaLaunchCooperativeKernel((void *)panel_qr_kernel<T>, dim3(G), dim3(256), args,
+                                             smem, st)) != cudaSuccess) return e;
+
+        // ---- two-sided update of A22 = a[r0:, r0:] (full symmetric storage)
+        T *A22 = a + r0 + (size_t)r0 * lda;
+        T *X = work;                      // m x b
+        T *W = work + (size_t)n * b;      // m x b
+        T *Y = work + (size_t)2 * n * b;  // b x b
+        T *Z = Y + (size_t)b * b;         // b x b
+        // X = A22 V
+        if ((e = gemm<T>(st, 0, 0, m, bw, m, T(1), A22, lda, V, n, T(0), W, m)) != cudaSuccess) return e;
+        // X = (A22 V) T
+        if ((e = gemm<T>(st, 0, 0, m, bw, bw, T(1), W, m, Tm, ldt, T(0), X, m)) != cudaSuccess) return e;
+        // Y = V^T X
+        if ((e = gemm<T>(st, 1, 0, bw, bw, m, T(1), V, n, X, m, T(0), Y, bw)) != cudaSuccess) return e;
+        // Z = T^T Y
+        if ((e = gemm<T>(st, 1, 0, bw, bw, bw, T(1), Tm, ldt, Y, bw, T(0), Z, bw)) != cudaSuccess) return e;
+        // W = X - 1/2 V Z
+        if ((e = cudaMemcpyAsync(W, X, sizeof(T) * (size_t)m * bw, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+        if ((e = gemm<T>(st, 0, 0, m, bw, bw, T(-0.5), V, n, Z, bw, T(1), W, m)) != cudaSuccess) return e;
+        // A22 -= V W^T + W V^T   (lower triangle), then mirror
+        if ((e = gemm<T>(st, 0, 1, m, m, bw, T(-1), V, n, W, m, T(1), A22, lda, 1)) != cudaSuccess) return e;
+        if ((e = gemm<T>(st, 0, 1, m, m, bw, T(-1), W, m, V, n, T(1), A22, lda, 1)) != cudaSuccess) return e;
+        if ((e = mirror_lower<T>(st, m, A22, lda)) != cudaSuccess) return e;
+    }
+    (void)work_elems;
+    return cudaSuccess;
+}
+
+template cudaError_t sy2sb<double>(cudaStream_t, int, int, double *, int, double *, double *,
+                                   double *, size_t, unsigned *, int *, int);
+template cudaError_t sy2sb<float>(cudaStream_t, int, int, float *, int, float *, float *,
+                                  float *, size_t, unsigned *, int *, int);
+
+}  // namespace egb

@@ -1,0 +1,216 @@
+// Symmetric tridiagonal eigensolver (step (3) of the two-stage method, arXiv:1705.11191
+// sec. 3.1), restricted to the wanted eigenpairs as the paper describes for KS-DFT.
+//
+//  * eigenvalues: Sturm-sequence bisection (Givens 1954; Barth, Martin & Wilkinson
+//    1967), one thread per wanted eigenvalue index;
+//  * eigenvectors: one twisted factorisation T - lambda I = N_r D_r N_r^T per
+//    eigenvalue (Parlett & Dhillon 1997/2000), which gives the vector with residual
+//    O(eps ||T||) in O(n) work; one thread per vector;
+//  * vectors of eigenvalues closer than 1e-5 ||T|| are re-orthogonalised (two passes of
+//    Gram-Schmidt within the cluster, as in inverse-iteration codes), which bounds the
+//    loss of orthogonality between any two returned vectors by about eps*1e5.
+// All of this runs in binary64 regardless of the precision of the reduction.
+#include <float.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace egb {
+
+__device__ __forceinline__ double guard_pivot(double q, double pivmin)
+{
+    return (fabs(q) < pivmin) ? -pivmin : q;
+}
+
+// number of eigenvalues < sigma
+__device__ int sturm_count(int n, const double *__restrict__ d, const double *__restrict__ e,
+                           double sigma, double pivmin)
+{
+    double q = guard_pivot(d[0] - sigma, pivmin);
+    int cnt = q < 0.0;
+    for (int i = 1; i < n; ++i) {
+        double ei = e[i - 1];
+        q = guard_pivot(d[i] - sigma - ei * ei / q, pivmin);
+        cnt += q < 0.0;
+    }
+    return cnt;
+}
+
+// [0]=gl, [1]=gu, [2]=pivmin, [3]=||T|| bound
+__global__ void gershgorin_kernel(int n, const double *d, const double *e, double *out)
+{
+    __shared__ double red[32];
+    double lo = DBL_MAX, hi = -DBL_MAX, e2max = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double r = 0.0;
+        if (i > 0) r += fabs(e[i - 1]);
+        if (i + 1 < n) { r += fabs(e[i]); e2max = fmax(e2max, e[i] * e[i]); }
+        lo = fmin(lo, d[i] - r);
+        hi = fmax(hi, d[i] + r);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        e2max = fmax(e2max, __shfl_xor_sync(0xffffffffu, e2max, o));
+    }
+    __shared__ double slo[32], shi[32], se[32];
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { slo[w] = lo; shi[w] = hi; se[w] = e2max; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            lo = fmin(lo, slo[q]); hi = fmax(hi, shi[q]); e2max = fmax(e2max, se[q]);
+        }
+        double tn = fmax(fabs(lo), fabs(hi));
+        double pad = 2.0 * DBL_EPSILON * tn * n + DBL_MIN;
+        out[0] = lo - pad;
+        out[1] = hi + pad;
+        out[2] = DBL_MIN * fmax(1.0, e2max);
+        out[3] = tn;
+    }
+    (void)red;
+}
+
+__global__ void bisect_kernel(int n, const double *d, const double *e, int count,
+                              const double *bounds, double *w)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= count) return;
+    double lo = bounds[0], hi = bounds[1], pivmin = bounds[2];
+    for (int it = 0; it < 128; ++it) {
+        double tol = 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin;
+        if (hi - lo <= tol) break;
+        double mid = 0.5 * (lo + hi);
+        if (sturm_count(n, d, e, mid, pivmin) <= idx) lo = mid; else hi = mid;
+    }
+    w[idx] = 0.5 * (lo + hi);
+}
+
+cudaError_t stebz(cudaStream_t st, int n, const double *d, const double *e, int count,
+                  double *w, int *status)
+{
+    (void)status;
+    if (n <= 0 || count <= 0) return cudaSuccess;
+    // bounds live after the count eigenvalues' scratch: caller passes w with room
+    // for count + 4 doubles
+    double *bounds = w + count;
+    gershgorin_kernel<<<1, 1024, 0, st>>>(n, d, e, bounds);
+    bisect_kernel<<<ceil_div(count, 64), 64, 0, st>>>(n, d, e, count, bounds, w);
+    return cudaGetLastError();
+}
+
+// Twisted factorisation eigenvector for each of the first kvec eigenvalues.
+template <typename T>
+__global__ void twisted_kernel(int n, const double *__restrict__ d, const double *__restrict__ e,
+                               int kvec, const double *__restrict__ w, const double *bounds,
+                               T *z, int ldz, double *dplus, double *uminus, int *status)
+{
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= kvec) return;
+    const double lam = w[l];
+    const double pivmin = bounds[2];
+    // forward: T - lam I = L+ D+ L+^T
+    double dp = guard_pivot(d[0] - lam, pivmin);
+    dplus[l] = dp;
+    for (int i = 0; i < n - 1; ++i) {
+        double lp = e[i] / dp;
+        dp = guard_pivot(d[i + 1] - lam - lp * e[i], pivmin);
+        dplus[(size_t)(i + 1) * kvec + l] = dp;
+    }
+    // backward: T - lam I = U- D- U-^T, twist index r = argmin |gamma_r|
+    double dm = guard_pivot(d[n - 1] - lam, pivmin);
+    double best = fabs(dplus[(size_t)(n - 1) * kvec + l] + dm - (d[n - 1] - lam));
+    int r = n - 1;
+    for (int i = n - 2; i >= 0; --i) {
+        double um = e[i] / dm;
+        uminus[(size_t)i * kvec + l] = um;
+        dm = guard_pivot(d[i] - lam - um * e[i], pivmin);
+        double g = fabs(dplus[(size_t)i * kvec + l] + dm - (d[i] - lam));
+        if (g < best) { best = g; r = i; }
+    }
+    // pass 1: norm of z (z_r = 1)
+    double nrm2 = 1.0, zi = 1.0;
+    for (int i = r - 1; i >= 0; --i) {
+        zi = -(e[i] / dplus[(size_t)i * kvec + l]) * zi;
+        nrm2 += zi * zi;
+    }
+    zi = 1.0;
+    for (int i = r; i < n - 1; ++i) {
+        zi = -uminus[(size_t)i * kvec + l] * zi;
+        nrm2 += zi * zi;
+    }
+    if (!(nrm2 < DBL_MAX)) { report_error(status, ELSI_ERR_NO_CONVERGENCE, l); nrm2 = 1.0; }
+    double s = 1.0 / sqrt(nrm2);
+    // pass 2: write z / ||z||
+    T *zc = z + (size_t)l * ldz;
+    zc[r] = (T)s;
+    zi = 1.0;
+    for (int i = r - 1; i >= 0; --i) {
+        zi = -(e[i] / dplus[(size_t)i * kvec + l]) * zi;
+        zc[i] = (T)(zi * s);
+    }
+    zi = 1.0;
+    for (int i = r; i < n - 1; ++i) {
+        zi = -uminus[(size_t)i * kvec + l] * zi;
+        zc[i + 1] = (T)(zi * s);
+    }
+}
+
+// One CTA per cluster start: Gram-Schmidt (two passes) within clusters of eigenvalues
+// closer than tol_rel * ||T||.
+template <typename T>
+__global__ void cluster_orth_kernel(int n, int kvec, const double *w, const double *bounds,
+                                    double tol_rel, T *z, int ldz, int *status)
+{
+    __shared__ double red[32];
+    const int i0 = blockIdx.x;
+    const double tol = tol_rel * fmax(bounds[3], DBL_MIN);
+    if (i0 > 0 && w[i0] - w[i0 - 1] < tol) return;  // not a cluster start
+    int i1 = i0 + 1;
+    while (i1 < kvec && w[i1] - w[i1 - 1] < tol) ++i1;
+    if (i1 - i0 < 2) return;
+    for (int v = i0 + 1; v < i1; ++v) {
+        T *zv = z + (size_t)v * ldz;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int u = i0; u < v; ++u) {
+                const T *zu = z + (size_t)u * ldz;
+                double s = 0.0;
+                for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)zu[i] * (double)zv[i];
+                s = block_sum(s, red);
+                for (int i = threadIdx.x; i < n; i += blockDim.x) zv[i] = (T)((double)zv[i] - s * (double)zu[i]);
+                __syncthreads();
+            }
+        }
+        double s = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)zv[i] * (double)zv[i];
+        s = block_sum(s, red);
+        if (s < 1e-4) {
+            if (threadIdx.x == 0) report_error(status, ELSI_ERR_NO_CONVERGENCE, v);
+            return;
+        }
+        double inv = 1.0 / sqrt(s);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) zv[i] = (T)((double)zv[i] * inv);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int kvec,
+                  const double *w, T *z, int ldz, double *scratch, int *cluster_ws, int *status)
+{
+    (void)cluster_ws;
+    if (n <= 0 || kvec <= 0) return cudaSuccess;
+    double *bounds = scratch + (size_t)2 * n * kvec;
+    gershgorin_kernel<<<1, 1024, 0, st>>>(n, d, e, bounds);
+    twisted_kernel<T><<<ceil_div(kvec, 64), 64, 0, st>>>(n, d, e, kvec, w, bounds, z, ldz, scratch,
+                                                        scratch + (size_t)n * kvec, status);
+    cluster_orth_kernel<T><<<kvec, 256, 0, st>>>(n, kvec, w, bounds, 1e-5, z, ldz, status);
+    return cudaGetLastError();
+}
+
+template cudaError_t stein<double>(cudaStream_t, int, const double *, const double *, int,
+                                   const double *, double *, int, double *, int *, int *);
+template cudaError_t stein<float>(cudaStream_t, int, const double *, const double *, int,
+                                  const double *, float *, int, double *, int *, int *);
+
+}  // namespace egb

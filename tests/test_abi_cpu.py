@@ -1,0 +1,67 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every
+function declared in include/elsi_gb.h, and rejects bad arguments before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1705_11191_gb300 as egb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "elsi_gb.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(elsi_\w+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1705_11191_gb300 import build
+    build.build()
+    return egb.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_init_rejects_bad_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.elsi_init(ctypes.byref(h), 2, 1, 2, 10, 5, 4.0) == 2   # libOMM: unsupported
+    assert lib.elsi_init(ctypes.byref(h), 1, 2, 2, 10, 5, 4.0) == 2   # CSC: unsupported
+    assert lib.elsi_init(ctypes.byref(h), 1, 1, 3, 10, 5, 4.0) == 1   # bad mode
+    assert lib.elsi_init(ctypes.byref(h), 1, 1, 2, 10, 11, 4.0) == 1  # n_state > n
+    assert lib.elsi_init(ctypes.byref(h), 1, 1, 2, 10, 2, 5.0) == 1   # too many electrons
+    assert lib.elsi_init(ctypes.byref(h), 1, 1, 2, 0, 1, 0.0) == 1
+
+
+def test_handle_lifecycle_and_setters(lib):
+    h = egb.Handle(16, 8, 8.0)
+    h.set_band_width(16)
+    h.set_broadening(egb.OCC_FERMI, 0.01)
+    h.set_occ_accuracy(1e-10)
+    h.set_mu_max_steps(50)
+    h.set_precision(egb.PREC_FP32_REFINE)
+    with pytest.raises(egb.ElsiError) as e:
+        h.set_broadening(3)  # Methfessel-Paxton
+    assert e.value.code == 2
+    with pytest.raises(egb.ElsiError):
+        h.set_band_width(7)
+    with pytest.raises(egb.ElsiError) as e:
+        h.get_mu()  # no dm solve yet
+    assert e.value.code == 8
+    h.close()
+    # use after finalize is rejected by the library
+    assert lib.elsi_set_band_width(ctypes.c_void_p(None), 16) == 8
+
+
+def test_stage_names(lib):
+    names = egb.stage_names()
+    assert names[0] == "cholesky" and "full_to_band" in names and "density" in names
