@@ -265,8 +265,10 @@ cudaError_t sb2st(cudaStream_t st, int n, int b, T *band, int ldb, double *d, do
         static bool attr_set[2] = {false, false};
         int ai = sizeof(T) == 8 ? 0 : 1;
         if (!attr_set[ai]) {
+            // opt in once for the largest band width (64)
+            const size_t smax = (2 * 64 * 64 + 2 * 64 + 2) * sizeof(T) + (64 + 4) * sizeof(double) + 16;
             if ((err = cudaFuncSetAttribute(chase_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem > 48 * 1024 ? (int)smem : 48 * 1024)) != cudaSuccess)
+                                            (int)smax)) != cudaSuccess)
                 return err;
             attr_set[ai] = true;
         }
@@ -393,8 +395,9 @@ cudaError_t apply_q2(cudaStream_t st, int n, int b, const T *v2, const T *tau2, 
     static bool attr_set[2] = {false, false};
     int ai = sizeof(T) == 8 ? 0 : 1;
     if (!attr_set[ai]) {
+        const size_t smax = ((size_t)kQ2Ring * kQ2Cols + (size_t)kQ2Sweeps * 64 + kQ2Sweeps) * sizeof(T);
         cudaError_t e = cudaFuncSetAttribute(apply_q2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem > 48 * 1024 ? (int)smem : 48 * 1024);
+                                             (int)smax);
         if (e != cudaSuccess) return e;
         attr_set[ai] = true;
     }
