@@ -1,0 +1,330 @@
+"""Benchmark: Kohn-Sham density-matrix solves per second, (H, S) -> (P, W), on one GB300.
+
+Workload: the 3D-cluster synthetic problem of n = 16384 basis functions (1093 atoms x 15
+functions, N_el = 4096, n_state = 2048, integer occupation, lambda_min(S) rescaled to
+>= 1e-2), inputs device-resident. One step = elsi_dm_real + elsi_get_edm_real through
+the C ABI, including the Cholesky of S (no reuse of the factor between steps). The
+FP32-reduction + refinement route is the measured arm; the binary64 route is timed
+beside it and both results are compared (relative Frobenius error of P).
+
+`--impl reference` times the FP64 CPU oracle instead (the paper has no runnable
+reference); under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("KS solves/s (H,S→P,W) at n=16384: FP32+refine vs FP64 GPU, rel err ≤1e-9")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# binary64 FMA rate of the chip, derived from unit counts: 152 SMs x 2 DFMA/clk/SM x 2 flop
+FP64_FLOP_PER_CLK = 152 * 2 * 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the binary64 comparison arm")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n: int):
+    import ksinputs
+    if n == 16384:
+        p = ksinputs.config(2)
+    elif n == 8192:
+        p = ksinputs.config(1)
+    else:
+        p = ksinputs.cluster_problem(n, seed=2)
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax or None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n_target: int, sample_n: int = 1024):
+    """Times the FP64 CPU oracle on a bounded sample (the same 3D-cluster construction at
+    sample_n) and scales its solve time by (n_target / sample_n)^3 to solves/s at n_target
+    (optimistic for the oracle: its Jacobi sweep count also grows with n)."""
+    import ksinputs
+    import oracle
+    oracle.build()
+    p = ksinputs.cluster_problem(sample_n, seed=2)
+    t0 = time.perf_counter()
+    oracle.solve(p.h, p.s, p.n_state, p.n_electron)
+    dt = time.perf_counter() - t0
+    scaled = dt * (n_target / sample_n) ** 3
+    return {"value": 1.0 / scaled, "unit": "solves/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"one full oracle solve at n={sample_n} (same 3D-cluster construction) "
+                      f"took {dt:.2f} s; scaled by (n/{sample_n})^3 to n={n_target}"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(args.warmup):
+        cpu_baseline(args.n)
+    for _ in range(args.steps):
+        steps.append(cpu_baseline(args.n))
+    val = sum(s["value"] for s in steps) / len(steps)
+    cb = dict(steps[-1])
+    cb["value"] = val
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / val, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"3D-cluster KS problem n={args.n}, N_el={args.n // 4}, "
+                                   f"n_state={args.n // 8}"},
+            "cpu_baseline": cb,
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def algorithmic_flops(n: int, k: int) -> float:
+    # Cholesky n^3/3, standard form ~n^3 (symmetric), full->band 4n^3/3, back-transforms
+    # through Q2, Q1 and L^-T for k vectors 5 n^2 k, P and W 2 n^2 k (8/3 n^3 + 7 n^2 k)
+    return 8.0 / 3.0 * n ** 3 + 7.0 * n * n * k
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import paper_1705_11191_gb300 as egb
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = egb.PREC_FP32_REFINE if args.precision == "fp32_refine" else egb.PREC_FP64
+    p = workload(args.n)
+    n, k = p.n, p.n_state
+    dev = torch.device("cuda", local)
+    H = torch.from_numpy(np.ascontiguousarray(p.h)).to(dev)
+    S = torch.from_numpy(np.ascontiguousarray(p.s)).to(dev)
+    P = torch.empty((n, n), dtype=torch.float64, device=dev)
+    W = torch.empty((n, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def make_handle(pr):
+        hd = egb.Handle(n, k, p.n_electron)
+        hd.set_stream(stream)
+        hd.set_precision(pr)
+        return hd
+
+    hd = make_handle(prec)
+
+    def step():
+        _, e = hd.dm_real(H, S, out=P)
+        hd.get_edm(out=W)
+        return e
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    stage_acc = {}
+    launches0 = egb.launch_count()
+    with ClockSampler(local) as cs:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            energy = step()
+            for kk, v in hd.stage_times().items():
+                stage_acc[kk] = stage_acc.get(kk, 0.0) + v
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = (egb.launch_count() - launches0) // args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    stages = {kk: v / args.steps for kk, v in stage_acc.items()}
+    iters, orth = hd.refine_info()
+    value = world * 1000.0 / ms
+
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64" if prec == egb.PREC_FP32_REFINE else "f64", "data": "synthetic",
+           "config": {"workload": f"3D-cluster KS problem n={n} (config 2), N_el={int(p.n_electron)}, "
+                                  f"n_state={k}, integer occupation, lambda_min(S)={p.lambda_min_s:.3g}",
+                      "precision": args.precision, "parallelism": f"replicas x{world}",
+                      "l2": "inputs (2 x 2.1 GB) larger than L2; no flush"},
+           "stages_ms": {kk: round(v, 3) for kk, v in stages.items()},
+           "refine_iters": iters, "orth_err": orth,
+           "tflops_algorithmic": algorithmic_flops(n, k) / (ms * 1e-3) / 1e12,
+           "clocks": cs.summary()}
+
+    # roofline of the dominant stage
+    dom = max(stages, key=stages.get)
+    out["roofline"] = roofline_for(dom, stages[dom], n, k, prec, out["clocks"])
+
+    # binary64 arm and the relative error of P between the two routes
+    if not args.no_fp64 and rank == 0 and prec == egb.PREC_FP32_REFINE:
+        h64 = make_handle(egb.PREC_FP64)
+        P64 = torch.empty_like(P)
+        h64.dm_real(H, S, out=P64)  # warm-up
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        _, e64 = h64.dm_real(H, S, out=P64)
+        W64 = h64.get_edm()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = t0.elapsed_time(t1)
+        relp = float(torch.linalg.norm(P - P64) / torch.linalg.norm(P64))
+        relw = float(torch.linalg.norm(W - W64) / torch.linalg.norm(W64))
+        out["fp64_gpu"] = {"value": 1000.0 / ms64, "unit": "solves/s", "ms_per_step": ms64,
+                           "stages_ms": {kk: round(v, 3) for kk, v in h64.stage_times().items()}}
+        out["rel_err_P_vs_fp64"] = relp
+        out["rel_err_W_vs_fp64"] = relw
+        out["abs_err_energy_vs_fp64"] = abs(energy - e64)
+        out["speedup_vs_fp64_gpu"] = ms64 / ms
+        h64.close()
+        del P64, W64
+
+    # end to end through the host-buffer entry point (pinned buffers)
+    if not args.no_e2e:
+        hh = torch.from_numpy(np.ascontiguousarray(p.h)).pin_memory()
+        sh = torch.from_numpy(np.ascontiguousarray(p.s)).pin_memory()
+        ph = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        wh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        hd.dm_real_host(hh, sh, ph, wh)
+        torch.cuda.synchronize()
+        e2e_steps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            hd.dm_real_host(hh, sh, ph, wh)
+        dt = (time.perf_counter() - t0) / e2e_steps
+        out["e2e"] = {"value": world / dt, "unit": "solves/s",
+                      "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": 2 * n * n * 8,
+                      "steps": e2e_steps}
+
+    out["gpu_launches"] = launches
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(n)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    hd.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def roofline_for(stage: str, stage_ms: float, n: int, k: int, prec: int, clocks: dict):
+    """Roofline entry for the dominant stage (algorithmic flops per launch of the stage /
+    its measured device time)."""
+    import math
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fp64_peak = FP64_FLOP_PER_CLK * 2070e6 / 1e12  # TFLOP/s at the maximum SM clock
+    flops = {
+        "cholesky": n ** 3 / 3.0,
+        "standard_form": 2.0 * n ** 3,
+        "full_to_band": 4.0 * n ** 3 / 3.0,
+        "back_q1": 2.0 * n * n * (n if prec == 1 else k),
+        "back_q2": 2.0 * n * n * (n if prec == 1 else k),
+        "back_subst": 1.0 * n * n * (n if prec == 1 else k),
+        "density": 2.0 * n * n * k,
+        "refine": 4.0 * n * n * k * 4 + 4.0 * n * k * k * 4,
+    }.get(stage)
+    if flops is None:
+        return {"bound": "latency", "stage": stage, "achieved": None, "peak": None,
+                "unit": None, "frac": None, "traffic": None}
+    achieved = flops / (stage_ms * 1e-3) / 1e12
+    if prec == 0 or stage == "refine":
+        return {"bound": "alu", "stage": stage, "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "peak_note": "binary64 FMA rate derived from 152 SMs x 2 DFMA/clk x 2070 MHz"}
+    fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12
+    return {"bound": "alu", "stage": stage, "achieved": achieved, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+            "peak_note": "binary32 FMA rate derived from 152 SMs x 128 FFMA/clk x 2070 MHz"}
+
+
+if __name__ == "__main__":
+    main()

@@ -130,6 +130,10 @@ const char *elsi_get_last_error(elsi_handle h);
 /* Library version string. */
 const char *elsi_gb_version(void);
 
+/* Number of CUDA kernels this library has launched in this process (all handles);
+ * a benchmarking aid, no counterpart in the paper. */
+long long elsi_gb_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,7 @@ def _declare(lib):
         "elsi_get_refine_info": ([H, _ip, _dp], i),
         "elsi_get_last_error": ([H], ctypes.c_char_p),
         "elsi_gb_version": ([], ctypes.c_char_p),
+        "elsi_gb_launch_count": ([], ctypes.c_longlong),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -88,6 +89,11 @@ def load(path: str | None = None):
             _declare(lib)
             _lib = lib
     return _lib
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().elsi_gb_launch_count())
 
 
 def _n_stages(lib) -> int:

@@ -93,6 +93,7 @@ static cudaError_t launch_potrf_diag(cudaStream_t st, int jb, T *a, int lda, T *
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    EGB_COUNT_LAUNCH();
     potrf_diag_kernel<T><<<1, 256, smem, st>>>(jb, a, lda, inv, ldi, status, base);
     return cudaGetLastError();
 }
@@ -122,6 +123,7 @@ cudaError_t potrf(cudaStream_t st, int n, T *a, int lda, T *inv_diag, T *work, i
     size_t total = (size_t)n * n;
     int grid = (int)((total + 255) / 256);
     if (grid > 152 * 16) grid = 152 * 16;
+    EGB_COUNT_LAUNCH();
     zero_upper_kernel<T><<<grid, 256, 0, st>>>(n, a, lda);
     return cudaGetLastError();
 }

@@ -7,9 +7,16 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <atomic>
+
 #include "elsi_gb.h"
 
 namespace egb {
+
+// Host-side count of the kernels this library has launched (reported through
+// elsi_gb_launch_count for benchmarking).
+extern std::atomic<long long> g_launches;
+#define EGB_COUNT_LAUNCH() (::egb::g_launches.fetch_add(1, std::memory_order_relaxed))
 
 // Device status word layout (one int array per handle, zeroed before each call):
 //   [0] first error code seen by any kernel (ELSI_ERR_*), 0 = none

@@ -81,6 +81,7 @@ cudaError_t occupation(cudaStream_t st, int k, const double *eps, double n_el, i
                        double kt, double occ_accuracy, int mu_max_steps, double *f, double *out,
                        int *status)
 {
+    EGB_COUNT_LAUNCH();
     occupation_kernel<<<1, 1024, 0, st>>>(k, eps, n_el, scheme, kt, occ_accuracy, mu_max_steps, f,
                                           out, status);
     return cudaGetLastError();
@@ -108,11 +109,13 @@ cudaError_t density_pw(cudaStream_t st, int n, int k, const T *c, int ldc, const
     int grid = (int)((total + 255) / 256);
     if (grid > 152 * 16) grid = 152 * 16;
     if (p) {
+        EGB_COUNT_LAUNCH();
         scale_columns_kernel<T><<<grid, 256, 0, st>>>(n, k, c, ldc, f, nullptr, cw);
         if ((e = gemm<T>(st, 0, 1, n, n, k, T(1), cw, n, c, ldc, T(0), p, n, 1)) != cudaSuccess) return e;
         if ((e = mirror_lower<T>(st, n, p, n)) != cudaSuccess) return e;
     }
     if (w) {
+        EGB_COUNT_LAUNCH();
         scale_columns_kernel<T><<<grid, 256, 0, st>>>(n, k, c, ldc, f, eps, cw);
         if ((e = gemm<T>(st, 0, 1, n, n, k, T(1), cw, n, c, ldc, T(0), w, n, 1)) != cudaSuccess) return e;
         if ((e = mirror_lower<T>(st, n, w, n)) != cudaSuccess) return e;

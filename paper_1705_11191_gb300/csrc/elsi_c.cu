@@ -16,6 +16,8 @@ using namespace egb;
 
 namespace egb {
 
+std::atomic<long long> g_launches{0};
+
 const char *const kStageNames[kNumStages] = {
     "cholesky",  "standard_form", "full_to_band", "band_to_tri", "tridiag_solve",
     "back_q2",   "back_q1",       "back_subst",   "refine",      "occupation",
@@ -56,6 +58,8 @@ static int check_handle(elsi_handle h)
 extern "C" {
 
 const char *elsi_gb_version(void) { return "elsi-gb300 0.1"; }
+
+long long elsi_gb_launch_count(void) { return egb::g_launches.load(); }
 
 int elsi_init(elsi_handle *out, int solver, int fmt, int mode, int n_basis, int n_state,
               double n_electron)

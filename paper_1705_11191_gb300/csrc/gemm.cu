@@ -13,8 +13,12 @@ template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 gemm_kernel(int m, int n, int k, T alpha, const T *__restrict__ A, int lda, int ta,
             const T *__restrict__ B, int ldb, int tb, T beta, T *__restrict__ C, int ldc,
-            int uplo)
+            int uplo, int kchunk, size_t cstride)
 {
+    // split-K: CTA z covers k in [z*kchunk, min(k, (z+1)*kchunk)) and writes C + z*cstride
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = min(k, kbeg + kchunk);
+    C += (size_t)blockIdx.z * cstride;
     constexpr int NT = (BM / TM) * (BN / TN);
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
@@ -33,7 +37,7 @@ gemm_kernel(int m, int n, int k, T alpha, const T *__restrict__ A, int lda, int 
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
 
-    for (int k0 = 0; k0 < k; k0 += BK) {
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
         // ---- stage op(A)[m0:m0+BM, k0:k0+BK] as As[kk][i]
 #pragma unroll
         for (int r = 0; r < (BM * BK + NT - 1) / NT; ++r) {
@@ -43,7 +47,7 @@ gemm_kernel(int m, int n, int k, T alpha, const T *__restrict__ A, int lda, int 
                 if (ta == 0) { i = e % BM; kk = e / BM; } else { kk = e % BK; i = e / BK; }
                 int gi = m0 + i, gk = k0 + kk;
                 T v = T(0);
-                if (gi < m && gk < k)
+                if (gi < m && gk < kend)
                     v = (ta == 0) ? A[(size_t)gi + (size_t)gk * lda] : A[(size_t)gk + (size_t)gi * lda];
                 As[kk][i] = v;
             }
@@ -57,7 +61,7 @@ gemm_kernel(int m, int n, int k, T alpha, const T *__restrict__ A, int lda, int 
                 if (tb == 0) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
                 int gj = n0 + j, gk = k0 + kk;
                 T v = T(0);
-                if (gj < n && gk < k)
+                if (gj < n && gk < kend)
                     v = (tb == 0) ? B[(size_t)gk + (size_t)gj * ldb] : B[(size_t)gj + (size_t)gk * ldb];
                 Bs[kk][j] = v;
             }
@@ -106,10 +110,57 @@ cudaError_t gemm(cudaStream_t st, int ta, int tb, int m, int n, int k, T alpha, 
     using G = GemmCfg<T>;
     dim3 grid(ceil_div(m, G::BM), ceil_div(n, G::BN));
     dim3 block((G::BM / G::TM) * (G::BN / G::TN));
+    EGB_COUNT_LAUNCH();
     gemm_kernel<T, G::BM, G::BN, G::BK, G::TM, G::TN><<<grid, block, 0, st>>>(
-        m, n, k, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, uplo);
+        m, n, k, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, uplo, k > 0 ? k : 1, 0);
     return cudaGetLastError();
 }
+
+template <typename T>
+__global__ void splitk_reduce_kernel(int m, int n, int splits, const T *part, T alpha, T *C, int ldc)
+{
+    size_t total = (size_t)m * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * total + e];
+        int i = (int)(e % m), j = (int)(e / m);
+        C[(size_t)i + (size_t)j * ldc] = alpha * s;
+    }
+}
+
+template <typename T>
+cudaError_t gemm_splitk(cudaStream_t st, int ta, int tb, int m, int n, int k, T alpha,
+                        const T *A, int lda, const T *B, int ldb, T *C, int ldc, T *part,
+                        size_t part_elems)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    using G = GemmCfg<T>;
+    const int tiles = ceil_div(m, G::BM) * ceil_div(n, G::BN);
+    int splits = ceil_div(2 * 152, tiles);
+    int maxs = k / 256;
+    if (splits > maxs) splits = maxs;
+    if ((size_t)splits * m * n > part_elems) splits = (int)(part_elems / ((size_t)m * n));
+    if (splits <= 1) return gemm<T>(st, ta, tb, m, n, k, alpha, A, lda, B, ldb, T(0), C, ldc, 0);
+    int kchunk = ceil_div(k, splits);
+    kchunk = ceil_div(kchunk, G::BK) * G::BK;
+    splits = ceil_div(k, kchunk);
+    dim3 grid(ceil_div(m, G::BM), ceil_div(n, G::BN), splits);
+    dim3 block((G::BM / G::TM) * (G::BN / G::TN));
+    EGB_COUNT_LAUNCH();
+    gemm_kernel<T, G::BM, G::BN, G::BK, G::TM, G::TN><<<grid, block, 0, st>>>(
+        m, n, k, T(1), A, lda, ta, B, ldb, tb, T(0), part, m, 0, kchunk, (size_t)m * n);
+    size_t total = (size_t)m * n;
+    int rg = (int)((total + 255) / 256);
+    if (rg > 152 * 8) rg = 152 * 8;
+    EGB_COUNT_LAUNCH();
+    splitk_reduce_kernel<T><<<rg, 256, 0, st>>>(m, n, splits, part, alpha, C, ldc);
+    return cudaGetLastError();
+}
+template cudaError_t gemm_splitk<double>(cudaStream_t, int, int, int, int, int, double, const double *,
+                                         int, const double *, int, double *, int, double *, size_t);
+template cudaError_t gemm_splitk<float>(cudaStream_t, int, int, int, int, int, float, const float *,
+                                        int, const float *, int, float *, int, float *, size_t);
 
 template cudaError_t gemm<double>(cudaStream_t, int, int, int, int, int, double, const double *,
                                   int, const double *, int, double, double *, int, int);
@@ -136,6 +187,7 @@ cudaError_t copy_matrix(cudaStream_t st, int m, int n, const Ts *src, int lds, T
     size_t total = (size_t)m * n;
     int grid = (int)((total + 255) / 256);
     if (grid > 152 * 32) grid = 152 * 32;
+    EGB_COUNT_LAUNCH();
     copy_matrix_kernel<Td, Ts><<<grid, 256, 0, st>>>(m, n, src, lds, dst, ldd);
     return cudaGetLastError();
 }
@@ -198,6 +250,7 @@ cudaError_t transpose(cudaStream_t st, int m, int n, const T *src, int lds, T *d
 {
     if (m <= 0 || n <= 0) return cudaSuccess;
     dim3 grid(ceil_div(m, 32), ceil_div(n, 32)), block(32, 8);
+    EGB_COUNT_LAUNCH();
     tile_transpose_kernel<T><<<grid, block, 0, st>>>(m, n, src, lds, dst, ldd, 0);
     return cudaGetLastError();
 }
@@ -207,6 +260,7 @@ cudaError_t mirror_lower(cudaStream_t st, int n, T *a, int lda)
 {
     if (n <= 0) return cudaSuccess;
     dim3 grid(ceil_div(n, 32), ceil_div(n, 32)), block(32, 8);
+    EGB_COUNT_LAUNCH();
     tile_transpose_kernel<T><<<grid, block, 0, st>>>(n, n, a, lda, a, lda, 1);
     return cudaGetLastError();
 }
@@ -216,6 +270,7 @@ cudaError_t symmetrize(cudaStream_t st, int n, T *a, int lda)
 {
     if (n <= 0) return cudaSuccess;
     dim3 grid(ceil_div(n, 32), ceil_div(n, 32)), block(32, 8);
+    EGB_COUNT_LAUNCH();
     tile_transpose_kernel<T><<<grid, block, 0, st>>>(n, n, a, lda, a, lda, 2);
     return cudaGetLastError();
 }
@@ -249,6 +304,7 @@ cudaError_t check_finite(cudaStream_t st, int m, int n, const T *a, int lda, int
     size_t total = (size_t)m * n;
     int grid = (int)((total + 255) / 256);
     if (grid > 152 * 16) grid = 152 * 16;
+    EGB_COUNT_LAUNCH();
     check_finite_kernel<T><<<grid, 256, 0, st>>>(m, n, a, lda, status);
     return cudaGetLastError();
 }

@@ -15,6 +15,13 @@ cudaError_t gemm(cudaStream_t st, int ta, int tb, int m, int n, int k, T alpha,
                  const T *A, int lda, const T *B, int ldb, T beta, T *C, int ldc,
                  int uplo = 0);
 
+// C = alpha * op(A) * op(B) with K split over several CTAs (for small outputs with a long
+// K); part: scratch of part_elems elements for the partial products.
+template <typename T>
+cudaError_t gemm_splitk(cudaStream_t st, int ta, int tb, int m, int n, int k, T alpha,
+                        const T *A, int lda, const T *B, int ldb, T *C, int ldc, T *part,
+                        size_t part_elems);
+
 // dst(m x n, ldd) = src(m x n, lds), with type conversion.
 template <typename Td, typename Ts>
 cudaError_t copy_matrix(cudaStream_t st, int m, int n, const Ts *src, int lds, Td *dst, int ldd);
@@ -70,8 +77,9 @@ cudaError_t extract_band(cudaStream_t st, int n, int b, const T *a, int lda, T *
 // Sturm bisection (w needs count + 4 entries: the Gershgorin bounds follow the values),
 // then eigenvectors of the first kvec of them into z (n x kvec, ldz) as type T.
 // scratch: 2*n*kvec + 8 doubles.
+// tol_rel: stop when the bracket is narrower than tol_rel * ||T|| (0: full binary64).
 cudaError_t stebz(cudaStream_t st, int n, const double *d, const double *e, int count,
-                  double *w, int *status);
+                  double *w, int *status, double tol_rel = 0.0);
 template <typename T>
 cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int kvec,
                   const double *w, T *z, int ldz, double *scratch, int *cluster_ws,

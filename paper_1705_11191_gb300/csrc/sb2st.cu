@@ -41,6 +41,7 @@ cudaError_t extract_band(cudaStream_t st, int n, int b, const T *a, int lda, T *
     size_t total = (size_t)ldb * n;
     int grid = (int)((total + 255) / 256);
     if (grid > 152 * 16) grid = 152 * 16;
+    EGB_COUNT_LAUNCH();
     extract_band_kernel<T><<<grid, 256, 0, st>>>(n, b, a, lda, band, ldb);
     return cudaGetLastError();
 }
@@ -57,19 +58,19 @@ struct ChaseArgs {
 // Householder vector for x (length L) in shared memory: on return x holds v (v[0]=1),
 // and the function returns tau; *beta_out receives the new leading entry.
 template <typename T>
-__device__ double house_smem(int L, T *x, double *red, double *beta_out)
+__device__ T house_smem(int L, T *x, T *red, T *beta_out)
 {
-    double ss = 0.0;
-    for (int i = 1 + threadIdx.x; i < L; i += blockDim.x) { double v = (double)x[i]; ss += v * v; }
+    T ss = T(0);
+    for (int i = 1 + threadIdx.x; i < L; i += blockDim.x) ss = fma(x[i], x[i], ss);
     ss = block_sum(ss, red);
-    double alpha = (double)x[0];
-    double tau = 0.0, beta = alpha;
-    if (ss != 0.0) {
-        double nrm = sqrt(alpha * alpha + ss);
-        beta = (alpha >= 0.0) ? -nrm : nrm;
+    T alpha = x[0];
+    T tau = T(0), beta = alpha;
+    if (ss != T(0)) {
+        T nrm = dsqrt<T>(alpha * alpha + ss);
+        beta = (alpha >= T(0)) ? -nrm : nrm;
         tau = (beta - alpha) / beta;
-        double scl = 1.0 / (alpha - beta);
-        for (int i = 1 + threadIdx.x; i < L; i += blockDim.x) x[i] = (T)((double)x[i] * scl);
+        T scl = T(1) / (alpha - beta);
+        for (int i = 1 + threadIdx.x; i < L; i += blockDim.x) x[i] = x[i] * scl;
     } else {
         for (int i = 1 + threadIdx.x; i < L; i += blockDim.x) x[i] = T(0);
     }
@@ -80,26 +81,25 @@ __device__ double house_smem(int L, T *x, double *red, double *beta_out)
     return tau;
 }
 
-// D (L x L, symmetric, ld ldd) <- H D H, H = I - tau v v^T. p, q: scratch of length L.
+// D (L x L, symmetric, ld ldd) <- H D H, H = I - tau v v^T. p: scratch of length L.
 template <typename T>
-__device__ void two_sided(int L, T *D, int ldd, const T *v, double tau, double *p, double *red)
+__device__ void two_sided(int L, T *D, int ldd, const T *v, T tau, T *p, T *red)
 {
-    if (tau == 0.0) return;
+    if (tau == T(0)) return;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < L; ++c) s += (double)D[i + c * ldd] * (double)v[c];
+        T s = T(0);
+        for (int c = 0; c < L; ++c) s = fma(D[i + c * ldd], v[c], s);
         p[i] = tau * s;
     }
     __syncthreads();
-    double part = 0.0;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) part += p[i] * (double)v[i];
-    double K = 0.5 * tau * block_sum(part, red);
-    for (int i = threadIdx.x; i < L; i += blockDim.x) p[i] -= K * (double)v[i];  // q
+    T part = T(0);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) part = fma(p[i], v[i], part);
+    T K = T(0.5) * tau * block_sum(part, red);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) p[i] -= K * v[i];  // q
     __syncthreads();
     for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
         int i = e % L, c = e / L;
-        double d = (double)D[i + c * ldd] - (double)v[i] * p[c] - p[i] * (double)v[c];
-        D[i + c * ldd] = (T)d;
+        D[i + c * ldd] = D[i + c * ldd] - v[i] * p[c] - p[i] * v[c];
     }
     __syncthreads();
 }
@@ -113,15 +113,14 @@ __device__ __forceinline__ T band_get(const T *band, int ldb, int r, int c)
 // One (sweep j, step t) task; all threads of the CTA take part.
 template <typename T>
 __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, int t, T *smem,
-                           double *red)
+                           T *red)
 {
     const int n = a.n, b = a.b, ldb = a.ldb;
     T *X = smem;                 // b x b (ld b)
     T *D = X + b * b;            // b x b (ld b)
     T *vnew = D + b * b;         // b
     T *vprev = vnew + b;         // b
-    double *p = reinterpret_cast<double *>(vprev + b + 2);  // b doubles (aligned below)
-    p = reinterpret_cast<double *>(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    T *p = vprev + b;            // b
     const int tid = threadIdx.x, nt = blockDim.x;
     size_t slot = (size_t)j * a.S + t;
 
@@ -129,10 +128,10 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
         const int L = min(b, n - 1 - j);
         for (int i = tid; i < b; i += nt) vnew[i] = (i < L) ? band[(size_t)(1 + i) + (size_t)j * ldb] : T(0);
         __syncthreads();
-        double beta;
-        double tau = house_smem<T>(L, vnew, red, &beta);
+        T beta;
+        T tau = house_smem<T>(L, vnew, red, &beta);
         for (int i = tid; i < L; i += nt)
-            band[(size_t)(1 + i) + (size_t)j * ldb] = (i == 0) ? (T)beta : T(0);
+            band[(size_t)(1 + i) + (size_t)j * ldb] = (i == 0) ? beta : T(0);
         // D = A[j+1 .. j+L]^2
         const int r0 = j + 1;
         for (int e = tid; e < L * L; e += nt) {
@@ -146,7 +145,7 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
             if (i >= c) band[(size_t)(i - c) + (size_t)(r0 + c) * ldb] = D[i + c * b];
         }
         for (int i = tid; i < b; i += nt) v2[slot * b + i] = (i < L) ? vnew[i] : T(0);
-        if (tid == 0) tau2[slot] = (T)tau;
+        if (tid == 0) tau2[slot] = tau;
         __syncthreads();
         return;
     }
@@ -155,7 +154,7 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     const int cb = r - b;  // first column of X
     size_t pslot = slot - 1;
     for (int i = tid; i < b; i += nt) vprev[i] = v2[pslot * b + i];
-    double taup = (double)tau2[pslot];
+    const T taup = tau2[pslot];
     // X = A[r .. r+L-1, cb .. cb+b-1]  (all strictly below the diagonal, distance 1..2b-1)
     for (int e = tid; e < L * b; e += nt) {
         int i = e % L, c = e / L;
@@ -163,39 +162,39 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     }
     __syncthreads();
     // X <- X H_prev : y = X v, X -= tau y v^T
-    if (taup != 0.0) {
+    if (taup != T(0)) {
         for (int i = tid; i < L; i += nt) {
-            double s = 0.0;
-            for (int c = 0; c < b; ++c) s += (double)X[i + c * b] * (double)vprev[c];
+            T s = T(0);
+            for (int c = 0; c < b; ++c) s = fma(X[i + c * b], vprev[c], s);
             p[i] = taup * s;
         }
         __syncthreads();
         for (int e = tid; e < L * b; e += nt) {
             int i = e % L, c = e / L;
-            X[i + c * b] = (T)((double)X[i + c * b] - p[i] * (double)vprev[c]);
+            X[i + c * b] = fma(-p[i], vprev[c], X[i + c * b]);
         }
         __syncthreads();
     }
     // new reflector from X[:, 0]
     for (int i = tid; i < b; i += nt) vnew[i] = (i < L) ? X[i] : T(0);
     __syncthreads();
-    double beta;
-    double tau = house_smem<T>(L, vnew, red, &beta);
+    T beta;
+    T tau = house_smem<T>(L, vnew, red, &beta);
     // left-apply to X[:, 1:]
-    if (tau != 0.0) {
+    if (tau != T(0)) {
         for (int c = 1 + tid; c < b; c += nt) {
-            double s = 0.0;
-            for (int i = 0; i < L; ++i) s += (double)vnew[i] * (double)X[i + c * b];
+            T s = T(0);
+            for (int i = 0; i < L; ++i) s = fma(vnew[i], X[i + c * b], s);
             p[c] = tau * s;
         }
         __syncthreads();
         for (int e = tid; e < L * (b - 1); e += nt) {
             int i = e % L, c = 1 + e / L;
-            X[i + c * b] = (T)((double)X[i + c * b] - (double)vnew[i] * p[c]);
+            X[i + c * b] = fma(-vnew[i], p[c], X[i + c * b]);
         }
         __syncthreads();
     }
-    if (tid == 0) X[0] = (T)beta;
+    if (tid == 0) X[0] = beta;
     for (int i = 1 + tid; i < L; i += nt) X[i] = T(0);
     __syncthreads();
     for (int e = tid; e < L * b; e += nt) {
@@ -214,7 +213,7 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
         if (i >= c) band[(size_t)(i - c) + (size_t)(r + c) * ldb] = D[i + c * b];
     }
     for (int i = tid; i < b; i += nt) v2[slot * b + i] = (i < L) ? vnew[i] : T(0);
-    if (tid == 0) tau2[slot] = (T)tau;
+    if (tid == 0) tau2[slot] = tau;
     __syncthreads();
 }
 
@@ -223,7 +222,7 @@ __global__ void __launch_bounds__(256) chase_kernel(T *band, T *v2, T *tau2, Cha
 {
     extern __shared__ unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
-    __shared__ double red[32];
+    __shared__ T red[32];
     const int n = a.n, b = a.b;
     const int nsweep = n - 2;  // sweeps j = 0 .. n-3
     for (long long time = 0; time <= a.tmax; ++time) {
@@ -261,12 +260,12 @@ cudaError_t sb2st(cudaStream_t st, int n, int b, T *band, int ldb, double *d, do
         a.n = n; a.b = b; a.ldb = ldb; a.S = S;
         a.tmax = 3ll * (n - 3) + (S - 1);
         a.count = sync; a.gen = sync + 1; a.status = status;
-        size_t smem = (2 * (size_t)b * b + 2 * b + 2) * sizeof(T) + (b + 4) * sizeof(double) + 16;
+        size_t smem = (2 * (size_t)b * b + 3 * b) * sizeof(T);
         static bool attr_set[2] = {false, false};
         int ai = sizeof(T) == 8 ? 0 : 1;
         if (!attr_set[ai]) {
             // opt in once for the largest band width (64)
-            const size_t smax = (2 * 64 * 64 + 2 * 64 + 2) * sizeof(T) + (64 + 4) * sizeof(double) + 16;
+            const size_t smax = (2 * 64 * 64 + 3 * 64) * sizeof(T);
             if ((err = cudaFuncSetAttribute(chase_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smax)) != cudaSuccess)
                 return err;
@@ -282,10 +281,12 @@ cudaError_t sb2st(cudaStream_t st, int n, int b, T *band, int ldb, double *d, do
         if (G < 1) G = 1;
         if ((err = cudaMemsetAsync(sync, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return err;
         void *args[] = {&band, &v2, &tau2, &a};
+        EGB_COUNT_LAUNCH();
         if ((err = cudaLaunchCooperativeKernel((void *)chase_kernel<T>, dim3(G), dim3(256), args, smem,
                                                st)) != cudaSuccess)
             return err;
     }
+    EGB_COUNT_LAUNCH();
     extract_tridiag_kernel<T><<<ceil_div(n, 256), 256, 0, st>>>(n, band, ldb, d, e);
     return cudaGetLastError();
 }
@@ -304,6 +305,8 @@ template cudaError_t sb2st<float>(cudaStream_t, int, int, float *, int, double *
 constexpr int kQ2Cols = 16;     // columns per CTA (2 per warp, 8 warps)
 constexpr int kQ2Sweeps = 64;   // m: sweeps per block
 constexpr int kQ2Ring = 256;    // ring rows (>= m + 2b - 1 for b <= 64)
+constexpr int kQ2RingLd = kQ2Ring + 16;  // per-column stride: the two columns of a warp use
+                                         // disjoint shared-memory banks
 
 template <typename T>
 __global__ void __launch_bounds__(256) apply_q2_kernel(int n, int b, int S, const T *__restrict__ v2,
@@ -311,8 +314,8 @@ __global__ void __launch_bounds__(256) apply_q2_kernel(int n, int b, int S, cons
                                                         int ldz)
 {
     extern __shared__ unsigned char smem_raw[];
-    T *ring = reinterpret_cast<T *>(smem_raw);          // kQ2Ring x kQ2Cols, [slot][col]
-    T *vs = ring + kQ2Ring * kQ2Cols;                   // m x b staged reflectors
+    T *ring = reinterpret_cast<T *>(smem_raw);          // kQ2Cols x kQ2RingLd, [col][slot]
+    T *vs = ring + kQ2RingLd * kQ2Cols;                 // m x b staged reflectors
     T *ts = vs + kQ2Sweeps * b;                         // m taus
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int col0 = blockIdx.x * kQ2Cols;
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(256) apply_q2_kernel(int n, int b, int S, cons
         int hi = min(n, Jend + b);                     // rows of step 0: up to (Jend-1)+1+b-1
         // initial load
         for (int r = lo + sub; r < hi; r += 16)
-            ring[(r % kQ2Ring) * kQ2Cols + lc] = col_ok ? z[(size_t)r + (size_t)gc * ldz] : T(0);
+            ring[lc * kQ2RingLd + (r % kQ2Ring)] = col_ok ? z[(size_t)r + (size_t)gc * ldz] : T(0);
         for (int t = 0; t < SJ; ++t) {
             // stage reflectors (j, t) for j in [J, Jend)
             __syncthreads();
@@ -349,19 +352,19 @@ __global__ void __launch_bounds__(256) apply_q2_kernel(int n, int b, int S, cons
             __syncthreads();
             for (int j = Jend - 1; j >= J; --j) {
                 const int jj = j - J;
-                const double tau = (double)ts[jj];
-                if (tau == 0.0) continue;
+                const T tau = ts[jj];
+                if (tau == T(0)) continue;
                 const int r0 = j + 1 + t * b;
                 const int L = min(b, n - r0);
                 if (L <= 0) continue;
-                double s = 0.0;
+                T s = T(0);
                 for (int i = sub; i < L; i += 16)
-                    s += (double)vs[jj * b + i] * (double)ring[((r0 + i) % kQ2Ring) * kQ2Cols + lc];
+                    s = fma(vs[jj * b + i], ring[lc * kQ2RingLd + ((r0 + i) % kQ2Ring)], s);
                 for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
                 s *= tau;
                 for (int i = sub; i < L; i += 16) {
-                    T &zr = ring[((r0 + i) % kQ2Ring) * kQ2Cols + lc];
-                    zr = (T)((double)zr - s * (double)vs[jj * b + i]);
+                    T &zr = ring[lc * kQ2RingLd + ((r0 + i) % kQ2Ring)];
+                    zr = fma(-s, vs[jj * b + i], zr);
                 }
                 __syncwarp();
             }
@@ -369,16 +372,16 @@ __global__ void __launch_bounds__(256) apply_q2_kernel(int n, int b, int S, cons
             int nlo = min(lo + b, n), nhi = min(hi + b, n);
             __syncwarp();
             for (int r = lo + sub; r < nlo; r += 16)
-                if (col_ok) z[(size_t)r + (size_t)gc * ldz] = ring[(r % kQ2Ring) * kQ2Cols + lc];
+                if (col_ok) z[(size_t)r + (size_t)gc * ldz] = ring[lc * kQ2RingLd + (r % kQ2Ring)];
             __syncwarp();
             for (int r = hi + sub; r < nhi; r += 16)
-                ring[(r % kQ2Ring) * kQ2Cols + lc] = col_ok ? z[(size_t)r + (size_t)gc * ldz] : T(0);
+                ring[lc * kQ2RingLd + (r % kQ2Ring)] = col_ok ? z[(size_t)r + (size_t)gc * ldz] : T(0);
             __syncwarp();
             lo = nlo;
             hi = nhi;
         }
         for (int r = lo + sub; r < hi; r += 16)
-            if (col_ok) z[(size_t)r + (size_t)gc * ldz] = ring[(r % kQ2Ring) * kQ2Cols + lc];
+            if (col_ok) z[(size_t)r + (size_t)gc * ldz] = ring[lc * kQ2RingLd + (r % kQ2Ring)];
         __syncwarp();
     }
 }
@@ -391,16 +394,17 @@ cudaError_t apply_q2(cudaStream_t st, int n, int b, const T *v2, const T *tau2, 
     if (n < 3 || k <= 0) return cudaSuccess;
     if (b > 64 || kQ2Sweeps + 2 * b - 1 > kQ2Ring) return cudaErrorInvalidValue;
     const int S = sb2st_steps(n, b);
-    size_t smem = ((size_t)kQ2Ring * kQ2Cols + (size_t)kQ2Sweeps * b + kQ2Sweeps) * sizeof(T);
+    size_t smem = ((size_t)kQ2RingLd * kQ2Cols + (size_t)kQ2Sweeps * b + kQ2Sweeps) * sizeof(T);
     static bool attr_set[2] = {false, false};
     int ai = sizeof(T) == 8 ? 0 : 1;
     if (!attr_set[ai]) {
-        const size_t smax = ((size_t)kQ2Ring * kQ2Cols + (size_t)kQ2Sweeps * 64 + kQ2Sweeps) * sizeof(T);
+        const size_t smax = ((size_t)kQ2RingLd * kQ2Cols + (size_t)kQ2Sweeps * 64 + kQ2Sweeps) * sizeof(T);
         cudaError_t e = cudaFuncSetAttribute(apply_q2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smax);
         if (e != cudaSuccess) return e;
         attr_set[ai] = true;
     }
+    EGB_COUNT_LAUNCH();
     apply_q2_kernel<T><<<ceil_div(k, kQ2Cols), 256, smem, st>>>(n, b, S, v2, tau2, k, z, ldz);
     return cudaGetLastError();
 }
@@ -425,7 +429,8 @@ cudaError_t apply_q1(cudaStream_t st, int n, int b, int k, const T *v1, const T 
         T *Y = work;                    // b x k
         T *Y2 = work + (size_t)b * k;   // b x k
         T *Zr = z + r0;
-        if ((e = gemm<T>(st, 1, 0, b, k, m, T(1), V, n, Zr, ldz, T(0), Y, b)) != cudaSuccess) return e;
+        if ((e = gemm_splitk<T>(st, 1, 0, b, k, m, T(1), V, n, Zr, ldz, Y, b, Y2 + (size_t)b * k,
+                                (size_t)16 * b * k)) != cudaSuccess) return e;
         if ((e = gemm<T>(st, 0, 0, b, k, b, T(1), Tm, b, Y, b, T(0), Y2, b)) != cudaSuccess) return e;
         if ((e = gemm<T>(st, 0, 0, m, k, b, T(-1), V, n, Y2, b, T(1), Zr, ldz)) != cudaSuccess) return e;
     }

@@ -48,7 +48,7 @@ static int ensure_workspace(elsi_gb_handle_s *h, int kz)
     size_t work = n * kTriBlock;
     size_t wsy = sy2sb_work_elems(h->n, b);
     if (wsy > work) work = wsy;
-    if ((size_t)2 * b * kz > work) work = (size_t)2 * b * kz;
+    if ((size_t)18 * b * kz > work) work = (size_t)18 * b * kz;
     ENSURE(work, double, work + 64);
     ENSURE(z, double, n * kz);
     ENSURE(d, double, n + 8);
@@ -59,6 +59,10 @@ static int ensure_workspace(elsi_gb_handle_s *h, int kz)
     ENSURE(stein, double, 2 * n * kz + 16);
     ENSURE(sync, unsigned, 64 + 2 * (1024 + 64 + 1024 * 64 + 1024 * 64 * 64));
     ENSURE(status, int, ST_WORDS);
+    if (h->precision == ELSI_PREC_FP32_REFINE) {
+        const size_t k = h->n_state;
+        ENSURE(rf, double, 5 * n * k + 2 * k * k + 1040 * k + 64);
+    }
     if (!w.status_host && cudaMallocHost((void **)&w.status_host, sizeof(int) * ST_WORDS) != cudaSuccess)
         return set_error(h, ELSI_ERR_NOMEM, "pinned status");
     if (!w.scal_host && cudaMallocHost((void **)&w.scal_host, sizeof(double) * 64) != cudaSuccess)
@@ -179,8 +183,20 @@ int run_solve(elsi_gb_handle_s *h, const SolveRequest &rq)
     Workspace &w = h->wk;
     cudaStream_t st = h->stream;
     CK(cudaMemsetAsync(w.status, 0, sizeof(int) * ST_WORDS, st));
-    if (h->precision == ELSI_PREC_FP64) rc = solve_fp64(h, rq);
-    else rc = solve_fp32_refine(h, rq);
+    if (h->precision == ELSI_PREC_FP64) {
+        rc = solve_fp64(h, rq);
+    } else {
+        rc = solve_fp32_refine(h, rq);
+        if (rc == ELSI_ERR_NO_CONVERGENCE) {
+            // The binary32 start was too far from the solution for the refinement (e.g. a
+            // badly conditioned S): solve the same problem along the binary64 route.
+            cudaStreamSynchronize(st);
+            CK(cudaMemsetAsync(w.status, 0, sizeof(int) * ST_WORDS, st));
+            h->have_l = false;
+            rc = solve_fp64(h, rq);
+            h->refine_iters = -1;
+        }
+    }
     if (rc) {
         cudaStreamSynchronize(st);
         return rc;

@@ -54,10 +54,10 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
     const int nref = min(bw, a.m);
     for (int j = 0; j < nref; ++j) {
         // ---- phase A: partial sum of squares below the diagonal of column j
-        double ss = 0.0;
+        T ssT = T(0);
         for (int i = tid; i < nrow; i += blockDim.x)
-            if (row0 + i > j) { double x = (double)Ploc[i * bwp + j]; ss += x * x; }
-        ss = block_sum(ss, red);
+            if (row0 + i > j) { T x = Ploc[i * bwp + j]; ssT = fma(x, x, ssT); }
+        double ss = block_sum((double)ssT, red);
         if (tid == 0) {
             a.part[g] = ss;
             if (j >= row0 && j < row0 + nrow) a.alpha[j] = (double)Ploc[(j - row0) * bwp + j];
@@ -75,22 +75,23 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             tau = (beta - alpha) / beta;
             scl = 1.0 / (alpha - beta);
         }
+        const T sclT = (T)scl;
         for (int i = tid; i < nrow; i += blockDim.x)
-            if (row0 + i > j) Ploc[i * bwp + j] = (T)((double)Ploc[i * bwp + j] * scl);
+            if (row0 + i > j) Ploc[i * bwp + j] = Ploc[i * bwp + j] * sclT;
         __syncthreads();
         // partial w_c = sum_i v_i P[i][c], c > j, over rows i >= j (v_j = 1)
         {
-            double s = 0.0;
+            T s = T(0);
             int c = tc;
             if (c > j && c < bw) {
                 for (int i = tr; i < nrow; i += 4) {
                     int gi = row0 + i;
                     if (gi < j) continue;
-                    double v = (gi == j) ? 1.0 : (double)Ploc[i * bwp + j];
-                    s += v * (double)Ploc[i * bwp + c];
+                    T v = (gi == j) ? T(1) : Ploc[i * bwp + j];
+                    s = fma(v, Ploc[i * bwp + c], s);
                 }
             }
-            colpart[tr][tc] = s;
+            colpart[tr][tc] = (double)s;
             __syncthreads();
             if (tid < bw)
                 a.wpart[(size_t)g * bw + tid] =
@@ -109,12 +110,12 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
         {
             int c = tc;
             if (c > j && c < bw) {
-                double wt = tau * wsum[c];
+                const T wt = (T)(tau * wsum[c]);
                 for (int i = tr; i < nrow; i += 4) {
                     int gi = row0 + i;
                     if (gi < j) continue;
-                    double v = (gi == j) ? 1.0 : (double)Ploc[i * bwp + j];
-                    Ploc[i * bwp + c] = (T)((double)Ploc[i * bwp + c] - v * wt);
+                    T v = (gi == j) ? T(1) : Ploc[i * bwp + j];
+                    Ploc[i * bwp + c] = fma(-v, wt, Ploc[i * bwp + c]);
                 }
             }
         }
@@ -139,16 +140,16 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
     // ---- Gram matrix V^T V (partial per CTA), then T by the forward recurrence
     for (int e = tid; e < bw * bw; e += blockDim.x) {
         int r = e % bw, c = e / bw;
-        double s = 0.0;
+        T s = T(0);
         if (r < nref && c < nref && r <= c) {
             for (int i = 0; i < nrow; ++i) {
                 int gi = row0 + i;
-                double vr = (gi > r) ? (double)Ploc[i * bwp + r] : (gi == r ? 1.0 : 0.0);
-                double vc = (gi > c) ? (double)Ploc[i * bwp + c] : (gi == c ? 1.0 : 0.0);
-                s += vr * vc;
+                T vr = (gi > r) ? Ploc[i * bwp + r] : (gi == r ? T(1) : T(0));
+                T vc = (gi > c) ? Ploc[i * bwp + c] : (gi == c ? T(1) : T(0));
+                s = fma(vr, vc, s);
             }
         }
-        a.gram[(size_t)g * bw * bw + e] = s;
+        a.gram[(size_t)g * bw * bw + e] = (double)s;
     }
     if (!grid_barrier(a.count, a.gen, G, a.status)) return;
     if (g != 0) return;
@@ -238,6 +239,7 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         T *Tm = t1 + (size_t)c0 * b;
         int ldt = b;
         void *args[] = {&P, &V, &Tm, &ldt, &pa};
+        EGB_COUNT_LAUNCH();
         if ((e = cudaLaunchCooperativeKernel((void *)panel_qr_kernel<T>, dim3(G), dim3(256), args,
                                              smem, st)) != cudaSuccess) return e;
 
@@ -252,7 +254,8 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         // X = (A22 V) T
         if ((e = gemm<T>(st, 0, 0, m, bw, bw, T(1), W, m, Tm, ldt, T(0), X, m)) != cudaSuccess) return e;
         // Y = V^T X
-        if ((e = gemm<T>(st, 1, 0, bw, bw, m, T(1), V, n, X, m, T(0), Y, bw)) != cudaSuccess) return e;
+        if ((e = gemm_splitk<T>(st, 1, 0, bw, bw, m, T(1), V, n, X, m, Y, bw, W,
+                                (size_t)n * b)) != cudaSuccess) return e;
         // Z = T^T Y
         if ((e = gemm<T>(st, 1, 0, bw, bw, bw, T(1), Tm, ldt, Y, bw, T(0), Z, bw)) != cudaSuccess) return e;
         // W = X - 1/2 V Z

@@ -71,31 +71,98 @@ __global__ void gershgorin_kernel(int n, const double *d, const double *e, doubl
     (void)red;
 }
 
-__global__ void bisect_kernel(int n, const double *d, const double *e, int count,
-                              const double *bounds, double *w)
+// number of eigenvalues < sigma, binary32 (used only to bracket)
+__device__ int sturm_count32(int n, const double *__restrict__ d, const double *__restrict__ e,
+                             float sigma, float pivmin)
 {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= count) return;
-    double lo = bounds[0], hi = bounds[1], pivmin = bounds[2];
-    for (int it = 0; it < 128; ++it) {
-        double tol = 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin;
-        if (hi - lo <= tol) break;
-        double mid = 0.5 * (lo + hi);
-        if (sturm_count(n, d, e, mid, pivmin) <= idx) lo = mid; else hi = mid;
+    float q = (float)d[0] - sigma;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    int cnt = q < 0.0f;
+    for (int i = 1; i < n; ++i) {
+        float ei = (float)e[i - 1];
+        q = (float)d[i] - sigma - __fdividef(ei * ei, q);
+        if (fabsf(q) < pivmin) q = -pivmin;
+        cnt += q < 0.0f;
     }
-    w[idx] = 0.5 * (lo + hi);
+    return cnt;
+}
+
+// Bisection for eigenvalue index idx = blockIdx.x * (blockDim.x / LANES) + group, with
+// LANES threads per eigenvalue evaluating LANES interior points of the current interval
+// (multisection: the interval shrinks by LANES + 1 per step).
+// Phase 1 (bracket32 != 0): binary32 counts down to a width of 1e-5 ||T||, then the
+// bracket is widened by 2e-5 ||T|| and checked with binary64 counts (falling back to the
+// Gershgorin interval if the check fails). Phase 2: binary64 counts down to
+// max(tol_rel * ||T||, 2 eps max|lo|,|hi|).
+template <int LANES>
+__global__ void bisect_kernel(int n, const double *d, const double *e, int count,
+                              const double *bounds, double *w, double tol_rel, int bracket32)
+{
+    const int group = threadIdx.x / LANES, lane = threadIdx.x % LANES;
+    const int idx = blockIdx.x * (blockDim.x / LANES) + group;
+    const unsigned gmask = (LANES == 32) ? 0xffffffffu
+                                         : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
+    const bool active = idx < count;
+    const double gl = bounds[0], gu = bounds[1], pivmin = bounds[2], tn = bounds[3];
+    double lo = gl, hi = gu;
+    if (bracket32 && active) {
+        float flo = (float)gl, fhi = (float)gu;
+        const float fpiv = fmaxf(1e-30f, (float)pivmin);
+        for (int it = 0; it < 64 && (double)(fhi - flo) > 1e-5 * tn; ++it) {
+            float sig = flo + (fhi - flo) * (float)(lane + 1) / (float)(LANES + 1);
+            int c = sturm_count32(n, d, e, sig, fpiv);
+            unsigned ok = __ballot_sync(gmask, c <= idx) & gmask;
+            int pcount = __popc(ok);
+            float nlo = __shfl_sync(gmask, sig, (threadIdx.x & 31) / LANES * LANES + max(pcount - 1, 0));
+            float nhi = __shfl_sync(gmask, sig, (threadIdx.x & 31) / LANES * LANES + min(pcount, LANES - 1));
+            if (pcount > 0) flo = nlo;
+            if (pcount < LANES) fhi = nhi;
+        }
+        lo = (double)flo - 2e-5 * tn;
+        hi = (double)fhi + 2e-5 * tn;
+        if (lo < gl) lo = gl;
+        if (hi > gu) hi = gu;
+        // verify the bracket in binary64: count(lo) <= idx < count(hi)
+        int c = sturm_count(n, d, e, lane == 0 ? lo : hi, pivmin);
+        int clo = __shfl_sync(gmask, c, (threadIdx.x & 31) / LANES * LANES);
+        int chi = (LANES > 1) ? __shfl_sync(gmask, c, (threadIdx.x & 31) / LANES * LANES + 1)
+                              : sturm_count(n, d, e, hi, pivmin);
+        if (!(clo <= idx && idx < chi)) { lo = gl; hi = gu; }
+    }
+    if (active) {
+        for (int it = 0; it < 128; ++it) {
+            double tol = fmax(tol_rel * tn, 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))) + 4.0 * pivmin;
+            if (hi - lo <= tol) break;
+            double sig = lo + (hi - lo) * (double)(lane + 1) / (double)(LANES + 1);
+            int c = sturm_count(n, d, e, sig, pivmin);
+            unsigned ok = __ballot_sync(gmask, c <= idx) & gmask;
+            int pcount = __popc(ok);
+            double nlo = __shfl_sync(gmask, sig, (threadIdx.x & 31) / LANES * LANES + max(pcount - 1, 0));
+            double nhi = __shfl_sync(gmask, sig, (threadIdx.x & 31) / LANES * LANES + min(pcount, LANES - 1));
+            if (pcount > 0) lo = nlo;
+            if (pcount < LANES) hi = nhi;
+        }
+        if (lane == 0) w[idx] = 0.5 * (lo + hi);
+    }
 }
 
 cudaError_t stebz(cudaStream_t st, int n, const double *d, const double *e, int count,
-                  double *w, int *status)
+                  double *w, int *status, double tol_rel)
 {
     (void)status;
     if (n <= 0 || count <= 0) return cudaSuccess;
-    // bounds live after the count eigenvalues' scratch: caller passes w with room
-    // for count + 4 doubles
+    // the Gershgorin bounds live right after the count eigenvalues (w has count + 4)
     double *bounds = w + count;
+    EGB_COUNT_LAUNCH();
     gershgorin_kernel<<<1, 1024, 0, st>>>(n, d, e, bounds);
-    bisect_kernel<<<ceil_div(count, 64), 64, 0, st>>>(n, d, e, count, bounds, w);
+    // enough threads to cover the latency: multisection when there are few eigenvalues
+    if (count <= 4096) {
+        EGB_COUNT_LAUNCH();
+        bisect_kernel<8><<<ceil_div(count, 16), 128, 0, st>>>(n, d, e, count, bounds, w, tol_rel, n > 512);
+    } else {
+        EGB_COUNT_LAUNCH();
+        bisect_kernel<2><<<ceil_div(count, 64), 128, 0, st>>>(n, d, e, count, bounds, w, tol_rel, 1);
+    }
     return cudaGetLastError();
 }
 
@@ -201,9 +268,12 @@ cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int 
     (void)cluster_ws;
     if (n <= 0 || kvec <= 0) return cudaSuccess;
     double *bounds = scratch + (size_t)2 * n * kvec;
+    EGB_COUNT_LAUNCH();
     gershgorin_kernel<<<1, 1024, 0, st>>>(n, d, e, bounds);
+    EGB_COUNT_LAUNCH();
     twisted_kernel<T><<<ceil_div(kvec, 64), 64, 0, st>>>(n, d, e, kvec, w, bounds, z, ldz, scratch,
                                                         scratch + (size_t)n * kvec, status);
+    EGB_COUNT_LAUNCH();
     cluster_orth_kernel<T><<<kvec, 256, 0, st>>>(n, kvec, w, bounds, 1e-5, z, ldz, status);
     return cudaGetLastError();
 }
