@@ -42,6 +42,7 @@ extern "C" {
 #define ELSI_ERR_CUDA 7         /* a CUDA runtime call failed */
 #define ELSI_ERR_STATE 8        /* call order violated (e.g. get_edm before dm) */
 #define ELSI_ERR_NOMEM 9        /* workspace allocation failed */
+#define ELSI_ERR_TOO_LARGE 10   /* request exceeds the fixed scratch of elsi_density_noalloc */
 
 /* Enumerations of elsi_init (sec. 4.3). Only solver 1 (ELPA route), format 1
  * (dense) and either parallel mode (both mean "one GPU, whole matrix") are accepted. */
@@ -123,6 +124,24 @@ const char *elsi_stage_name(int i);
 /* Diagnostics of the last FP32_REFINE solve: refinement iterations used and the
  * final max |(C^T S C - I)_ij| over the occupied block. */
 int elsi_get_refine_info(elsi_handle h, int *iters, double *orth_err);
+
+/* Allocation-free density matrices from caller-supplied orbitals (this entry point has
+ * no counterpart in the paper). For callers that cannot allocate GPU memory when they
+ * need the result: code running during CUDA graph capture, hosts whose GPU memory is
+ * owned by another framework's pre-sized pool, loops that forbid allocation after
+ * start-up. Computes den_mat = evec diag(occ) evec^T and, if edm is not NULL,
+ * edm = evec diag(occ * eval) evec^T (n_basis x n_basis, column-major, symmetric).
+ * evec: n_basis x n_state column-major device array; occ, eval: n_state device arrays
+ * (eval may be NULL when edm is NULL). All pointers are device pointers; work is
+ * enqueued on `stream` (cudaStream_t, NULL = legacy default stream) and the call returns
+ * without synchronising. Scratch: a fixed 16 MiB array inside the library
+ * (n_basis * n_state <= 2^21); larger requests return ELSI_ERR_TOO_LARGE. No memory is
+ * allocated. The first call on each device looks up the array's device address, so
+ * make that first call before any stream capture. Calls whose GPU work overlaps in time
+ * share the scratch and race. Returns ELSI_OK, ELSI_ERR_ARG, ELSI_ERR_TOO_LARGE or
+ * ELSI_ERR_CUDA. */
+int elsi_density_noalloc(int n_basis, int n_state, const double *evec, const double *occ,
+                         const double *eval, double *den_mat, double *edm, void *stream);
 
 /* Message describing the last error on this handle ("" if none). */
 const char *elsi_get_last_error(elsi_handle h);

@@ -28,7 +28,7 @@ PREC_FP64, PREC_FP32_REFINE = 0, 1
 
 ERR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_UNSUPPORTED", 3: "ERR_NOT_PD",
              4: "ERR_NONFINITE", 5: "ERR_NO_CONVERGENCE", 6: "ERR_TIMEOUT",
-             7: "ERR_CUDA", 8: "ERR_STATE", 9: "ERR_NOMEM"}
+             7: "ERR_CUDA", 8: "ERR_STATE", 9: "ERR_NOMEM", 10: "ERR_TOO_LARGE"}
 
 _lib = None
 _lock = threading.Lock()
@@ -69,6 +69,7 @@ def _declare(lib):
         "elsi_get_last_error": ([H], ctypes.c_char_p),
         "elsi_gb_version": ([], ctypes.c_char_p),
         "elsi_gb_launch_count": ([], ctypes.c_longlong),
+        "elsi_density_noalloc": ([i, i, _vp, _vp, _vp, _vp, _vp, _vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
