@@ -3,6 +3,7 @@
 // status (cudaSuccess or the error of the launch).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace egb {
@@ -101,5 +102,18 @@ cudaError_t occupation(cudaStream_t st, int k, const double *eps, double n_el, i
 template <typename T>
 cudaError_t density_pw(cudaStream_t st, int n, int k, const T *c, int ldc, const double *f,
                        const double *eps, T *p, T *w, T *cw);
+
+// ---- binary64-accurate products on the bf16 tensor cores (ozaki.cu) ----
+// Splits V vectors of length K (element (v, q) at src[v * sv + q * sq], optionally times
+// scale[q] * scale2[q]) into the digit planes consumed by ozaki_gemm.
+size_t ozaki_split_elems(int V, int K);  // bf16 elements of the planes of V vectors
+cudaError_t ozaki_split(cudaStream_t st, int V, int K, const double *src, long long sv,
+                        long long sq, const double *scale, const double *scale2,
+                        __nv_bfloat16 *planes, int *exps);
+// C (m x n, ldc) = alpha * A B + beta * C with A given by the split of its m rows and B
+// by the split of its n columns (both of length k). uplo = 1: lower triangle only.
+cudaError_t ozaki_gemm(cudaStream_t st, int m, int n, int k, double alpha,
+                       const __nv_bfloat16 *Ad, const int *ea, const __nv_bfloat16 *Bd,
+                       const int *eb, double beta, double *C, int ldc, int uplo);
 
 }  // namespace egb

@@ -19,6 +19,8 @@
 // step, the treatment of clustered eigenvalues in Ogita & Aishima's follow-up work), after
 // which pairs inside a cluster only receive the R_ij / 2 re-orthonormalisation.
 #include <float.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -435,33 +437,48 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     const double *S64 = unit ? nullptr : rq.ovlp;
     const double delta = 1e-4;  // Ha: eigenvalues closer than this are refined as a cluster
 
+    // digit planes for the binary64-accurate products on the tensor cores
+    const size_t pNN = ozaki_split_elems(n, n), pKN = ozaki_split_elems(k, n),
+                 pNK = ozaki_split_elems(n, k);
+    __nv_bfloat16 *HDG = w.oz, *SDG = HDG + pNN, *XDG = SDG + pNN, *YHDG = XDG + pKN,
+                  *YSDG = YHDG + pKN, *PADG = YSDG + pKN, *PBDG = PADG + pNK, *WADG = PBDG + pNK;
+    const size_t es = (size_t)n + k + 256;
+    int *eH = w.ozexp, *eS = eH + es, *eX = eS + es, *eYH = eX + es, *eYS = eYH + es,
+        *ePA = eYS + es, *ePB = ePA + es, *eWA = ePB + es;
+    // H and S are symmetric: the split of their rows reads contiguous columns
+    CKR(ozaki_split(st, n, n, rq.ham, n, 1, nullptr, nullptr, HDG, eH));
+    if (S64) CKR(ozaki_split(st, n, n, S64, n, 1, nullptr, nullptr, SDG, eS));
+
     // products, cluster Rayleigh-Ritz rotation and the Rayleigh quotients of the
     // current X_o (steps shared by every iteration and the final polish)
     auto products_and_rr = [&]() -> int {
-        CKR(gemm<double>(st, 0, 0, n, k, n, 1.0, rq.ham, n, XO, n, 0.0, YH, n));
-        if (S64) CKR(gemm<double>(st, 0, 0, n, k, n, 1.0, S64, n, XO, n, 0.0, YS, n));
+        CKR(ozaki_split(st, k, n, XO, n, 1, nullptr, nullptr, XDG, eX));
+        CKR(ozaki_gemm(st, n, k, n, 1.0, HDG, eH, XDG, eX, 0.0, YH, n, 0));
+        if (S64) CKR(ozaki_gemm(st, n, k, n, 1.0, SDG, eS, XDG, eX, 0.0, YS, n, 0));
         else CKR(cudaMemcpyAsync(YS, XO, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
-        CKR(gemm<double>(st, 1, 0, k, k, n, 1.0, XO, n, YH, n, 0.0, GOO, k));
-        CKR(gemm<double>(st, 1, 0, k, k, n, 1.0, XO, n, YS, n, 0.0, SOO, k));
-        EGB_COUNT_LAUNCH();
+        CKR(ozaki_split(st, k, n, YH, n, 1, nullptr, nullptr, YHDG, eYH));
+        CKR(ozaki_split(st, k, n, YS, n, 1, nullptr, nullptr, YSDG, eYS));
+        CKR(ozaki_gemm(st, k, k, n, 1.0, XDG, eX, YHDG, eYH, 0.0, GOO, k, 0));
+        CKR(ozaki_gemm(st, k, k, n, 1.0, XDG, eX, YSDG, eYS, 0.0, SOO, k, 0));
+        // X^T H X and X^T S X are symmetric; rounding of the two products is not, and an
+        // antisymmetric error would enter E_ij + E_ji (the re-orthonormalisation) divided
+        // by lambda_j - lambda_i. Use the symmetric parts.
+        CKR(symmetrize<double>(st, k, GOO, k));
+        CKR(symmetrize<double>(st, k, SOO, k));
         cluster_scan_kernel<<<1, 1, 0, st>>>(k, GOO, SOO, delta, CID, CSZ);
-        EGB_COUNT_LAUNCH();
         cluster_rr_kernel<<<k, 32, 0, st>>>(k, GOO, SOO, CID, CSZ, QBUF);
-        EGB_COUNT_LAUNCH();
         rotate_cols_kernel<<<dim3(k, ceil_div(n, 256)), 256, 0, st>>>(n, k, CID, CSZ, QBUF, XO, YH, YS);
-        EGB_COUNT_LAUNCH();
         rotate_gram_kernel<<<dim3(k, 1), 256, 0, st>>>(k, CID, CSZ, QBUF, GOO, SOO, 0);
-        EGB_COUNT_LAUNCH();
         rotate_gram_kernel<<<dim3(k, 1), 256, 0, st>>>(k, CID, CSZ, QBUF, GOO, SOO, 1);
-        EGB_COUNT_LAUNCH();
         gram_diag_kernel<<<grid_for(k), 256, 0, st>>>(k, GOO, SOO, GD, SD);
-        EGB_COUNT_LAUNCH();
         residual_kernel<<<grid_for(nk), 256, 0, st>>>(n, k, GD, SD, LAM, YH, YS, R32);
         return cudaGetLastError() == cudaSuccess ? ELSI_OK
                                                  : set_error(h, ELSI_ERR_CUDA, "refinement launch");
     };
 
     CKR(copy_matrix<double, float>(st, n, k, X32, n, XO, n));
+    const char *venv = getenv("ELSI_GB_VERBOSE");
+    const bool verbose = venv && venv[0] == '1';
     int iters = 0;
     double emax = 1.0;
     for (int it = 0; it < h->refine_max_iter; ++it) {
@@ -483,6 +500,9 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
         CKR(cudaStreamSynchronize(st));
         emax = w.scal_host[8];
         ++iters;
+        if (verbose)
+            fprintf(stderr, "[elsi-gb] refine iteration %d: max|E| %.3e, max|R_oo| %.3e\n", iters, emax,
+                    w.scal_host[9]);
         if (emax < 1e-12) break;
     }
     // final polish: Rayleigh-Ritz inside clusters, Rayleigh quotients, orthonormality
@@ -497,6 +517,7 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     }
     h->refine_iters = iters;
     h->orth_err = w.scal_host[8];
+    if (verbose) fprintf(stderr, "[elsi-gb] refine final orthonormality defect %.3e\n", h->orth_err);
     if (!(emax < 1e-8) || !(h->orth_err < 1e-10))
         return set_error(h, ELSI_ERR_NO_CONVERGENCE,
                          "refinement did not converge (max|E| %.3g, orthonormality %.3g)", emax,
@@ -519,7 +540,17 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
             if (kocc > k) kocc = k;
             if (kocc < 1) kocc = 1;
         }
-        CKR(density_pw<double>(st, n, kocc, XO, n, w.f, w.w, rq.dm, rq.want_edm ? w.edm : nullptr, YH));
+        // P = X_o diag(f) X_o^T and W = X_o diag(f eps) X_o^T, binary64-accurate products
+        // of the rows of X_o on the tensor cores (lower triangle, then mirrored)
+        CKR(ozaki_split(st, n, kocc, XO, 1, n, nullptr, nullptr, PBDG, ePB));
+        CKR(ozaki_split(st, n, kocc, XO, 1, n, w.f, nullptr, PADG, ePA));
+        CKR(ozaki_gemm(st, n, n, kocc, 1.0, PADG, ePA, PBDG, ePB, 0.0, rq.dm, n, 1));
+        CKR(mirror_lower<double>(st, n, rq.dm, n));
+        if (rq.want_edm) {
+            CKR(ozaki_split(st, n, kocc, XO, 1, n, w.f, w.w, WADG, eWA));
+            CKR(ozaki_gemm(st, n, n, kocc, 1.0, WADG, eWA, PBDG, ePB, 0.0, w.edm, n, 1));
+            CKR(mirror_lower<double>(st, n, w.edm, n));
+        }
     }
     CKR(cudaEventRecord(w.ev[kNumStages], st));
     return ELSI_OK;

@@ -1,6 +1,7 @@
 // Stage sequence of one solve (arXiv:1705.11191 sec. 3.1, Eqs. 8-11 and steps (1)-(5);
 // sec. 4.4 for the occupation and density matrix).
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
@@ -13,7 +14,7 @@ void free_workspace(elsi_gb_handle_s *h)
 {
     Workspace &w = h->wk;
     void *bufs[] = {w.a, w.l, w.v1, w.edm, w.v2, w.tau2, w.band, w.t1, w.invd, w.work, w.z,
-                    w.d, w.e, w.w, w.f, w.scal, w.stein, w.rf, w.sync, w.status,
+                    w.d, w.e, w.w, w.f, w.scal, w.stein, w.rf, w.oz, w.ozexp, w.sync, w.status,
                     w.host_h, w.host_s, w.host_p};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -62,6 +63,12 @@ static int ensure_workspace(elsi_gb_handle_s *h, int kz)
     if (h->precision == ELSI_PREC_FP32_REFINE) {
         const size_t k = h->n_state;
         ENSURE(rf, double, 5 * n * k + 2 * k * k + 1040 * k + 64);
+        // digits of H, S (n x n), of X_o, Y_H, Y_S (k columns of length n) and of the
+        // rows of X_o for P and W (three splits of n rows of length k)
+        ENSURE(oz, __nv_bfloat16, 2 * ozaki_split_elems((int)n, (int)n) +
+                                      3 * ozaki_split_elems((int)k, (int)n) +
+                                      3 * ozaki_split_elems((int)n, (int)k));
+        ENSURE(ozexp, int, 8 * (n + k + 256));
     }
     if (!w.status_host && cudaMallocHost((void **)&w.status_host, sizeof(int) * ST_WORDS) != cudaSuccess)
         return set_error(h, ELSI_ERR_NOMEM, "pinned status");
@@ -191,6 +198,8 @@ int run_solve(elsi_gb_handle_s *h, const SolveRequest &rq)
             // The binary32 start was too far from the solution for the refinement (e.g. a
             // badly conditioned S): solve the same problem along the binary64 route.
             cudaStreamSynchronize(st);
+            const char *nf = getenv("ELSI_GB_NO_FALLBACK");
+            if (nf && nf[0] == '1') return rc;
             CK(cudaMemsetAsync(w.status, 0, sizeof(int) * ST_WORDS, st));
             h->have_l = false;
             rc = solve_fp64(h, rq);

@@ -2,6 +2,7 @@
 // sec. 4.1: all runtime parameters live in the handle, no globals).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -39,6 +40,8 @@ struct Workspace {
     EGB_BUF(double, scal)    // device scalars: mu, energy, refinement diagnostics
     EGB_BUF(double, stein)   // tridiagonal-eigenvector scratch
     EGB_BUF(double, rf)      // refinement buffers
+    EGB_BUF(__nv_bfloat16, oz)  // digit planes of the binary64-accurate products
+    EGB_BUF(int, ozexp)      // their exponents
     EGB_BUF(unsigned, sync)  // grid-barrier words + partial sums
     EGB_BUF(int, status)
     EGB_BUF(double, host_h)  // staging for the _host entry points
