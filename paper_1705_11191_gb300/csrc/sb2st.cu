@@ -81,17 +81,44 @@ __device__ T house_smem(int L, T *x, T *red, T *beta_out)
     return tau;
 }
 
+// out[i] = scale * sum_{c < nc} M[i + c * ldm] v[c] for i < L (L <= 64), four lanes per
+// row (columns c = part + 4j), blockDim.x == 256. Ends with __syncthreads().
+template <typename T>
+__device__ __forceinline__ void rows_dot(int L, int nc, const T *M, int ldm, const T *v, T scale,
+                                         T *out)
+{
+    const int row = threadIdx.x >> 2, part = threadIdx.x & 3;
+    T s = T(0);
+    if (row < L)
+        for (int c = part; c < nc; c += 4) s = fma(M[row + c * ldm], v[c], s);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (part == 0 && row < L) out[row] = scale * s;
+    __syncthreads();
+}
+
+// out[c] = scale * sum_{i < L} v[i] M[i + c * ldm] for c0 <= c < nc (nc <= 64), four lanes per
+// column (rows i = part + 4j). Ends with __syncthreads().
+template <typename T>
+__device__ __forceinline__ void cols_dot(int L, int c0, int nc, const T *M, int ldm, const T *v,
+                                         T scale, T *out)
+{
+    const int c = threadIdx.x >> 2, part = threadIdx.x & 3;
+    T s = T(0);
+    if (c >= c0 && c < nc)
+        for (int i = part; i < L; i += 4) s = fma(v[i], M[i + c * ldm], s);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (part == 0 && c >= c0 && c < nc) out[c] = scale * s;
+    __syncthreads();
+}
+
 // D (L x L, symmetric, ld ldd) <- H D H, H = I - tau v v^T. p: scratch of length L.
 template <typename T>
 __device__ void two_sided(int L, T *D, int ldd, const T *v, T tau, T *p, T *red)
 {
     if (tau == T(0)) return;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        T s = T(0);
-        for (int c = 0; c < L; ++c) s = fma(D[i + c * ldd], v[c], s);
-        p[i] = tau * s;
-    }
-    __syncthreads();
+    rows_dot<T>(L, L, D, ldd, v, tau, p);  // p = tau D v
     T part = T(0);
     for (int i = threadIdx.x; i < L; i += blockDim.x) part = fma(p[i], v[i], part);
     T K = T(0.5) * tau * block_sum(part, red);
@@ -110,15 +137,18 @@ __device__ __forceinline__ T band_get(const T *band, int ldb, int r, int c)
     return (r >= c) ? band[(size_t)(r - c) + (size_t)c * ldb] : band[(size_t)(c - r) + (size_t)r * ldb];
 }
 
-// One (sweep j, step t) task; all threads of the CTA take part.
+// One (sweep j, step t) task; all threads of the CTA take part. The b x b tiles use the
+// leading dimension b + 8, which makes the four-lanes-per-row dot products
+// conflict-free in shared memory.
 template <typename T>
 __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, int t, T *smem,
                            T *red)
 {
     const int n = a.n, b = a.b, ldb = a.ldb;
-    T *X = smem;                 // b x b (ld b)
-    T *D = X + b * b;            // b x b (ld b)
-    T *vnew = D + b * b;         // b
+    const int ld = b + 8;
+    T *X = smem;                 // b x b (ld)
+    T *D = X + b * ld;           // b x b (ld)
+    T *vnew = D + b * ld;        // b
     T *vprev = vnew + b;         // b
     T *p = vprev + b;            // b
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -126,23 +156,22 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
 
     if (t == 0) {
         const int L = min(b, n - 1 - j);
+        const int r0 = j + 1;
         for (int i = tid; i < b; i += nt) vnew[i] = (i < L) ? band[(size_t)(1 + i) + (size_t)j * ldb] : T(0);
+        // D = A[j+1 .. j+L]^2
+        for (int e = tid; e < L * L; e += nt) {
+            int i = e % L, c = e / L;
+            D[i + c * ld] = band_get(band, ldb, r0 + i, r0 + c);
+        }
         __syncthreads();
         T beta;
         T tau = house_smem<T>(L, vnew, red, &beta);
         for (int i = tid; i < L; i += nt)
             band[(size_t)(1 + i) + (size_t)j * ldb] = (i == 0) ? beta : T(0);
-        // D = A[j+1 .. j+L]^2
-        const int r0 = j + 1;
+        two_sided<T>(L, D, ld, vnew, tau, p, red);
         for (int e = tid; e < L * L; e += nt) {
             int i = e % L, c = e / L;
-            D[i + c * b] = band_get(band, ldb, r0 + i, r0 + c);
-        }
-        __syncthreads();
-        two_sided<T>(L, D, b, vnew, tau, p, red);
-        for (int e = tid; e < L * L; e += nt) {
-            int i = e % L, c = e / L;
-            if (i >= c) band[(size_t)(i - c) + (size_t)(r0 + c) * ldb] = D[i + c * b];
+            if (i >= c) band[(size_t)(i - c) + (size_t)(r0 + c) * ldb] = D[i + c * ld];
         }
         for (int i = tid; i < b; i += nt) v2[slot * b + i] = (i < L) ? vnew[i] : T(0);
         if (tid == 0) tau2[slot] = tau;
@@ -158,20 +187,20 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     // X = A[r .. r+L-1, cb .. cb+b-1]  (all strictly below the diagonal, distance 1..2b-1)
     for (int e = tid; e < L * b; e += nt) {
         int i = e % L, c = e / L;
-        X[i + c * b] = band[(size_t)(r + i - (cb + c)) + (size_t)(cb + c) * ldb];
+        X[i + c * ld] = band[(size_t)(r + i - (cb + c)) + (size_t)(cb + c) * ldb];
+    }
+    // D = A[r .. r+L-1]^2 (read now: the task's window is not touched by anyone else)
+    for (int e = tid; e < L * L; e += nt) {
+        int i = e % L, c = e / L;
+        D[i + c * ld] = band_get(band, ldb, r + i, r + c);
     }
     __syncthreads();
     // X <- X H_prev : y = X v, X -= tau y v^T
     if (taup != T(0)) {
-        for (int i = tid; i < L; i += nt) {
-            T s = T(0);
-            for (int c = 0; c < b; ++c) s = fma(X[i + c * b], vprev[c], s);
-            p[i] = taup * s;
-        }
-        __syncthreads();
+        rows_dot<T>(L, b, X, ld, vprev, taup, p);
         for (int e = tid; e < L * b; e += nt) {
             int i = e % L, c = e / L;
-            X[i + c * b] = fma(-p[i], vprev[c], X[i + c * b]);
+            X[i + c * ld] = fma(-p[i], vprev[c], X[i + c * ld]);
         }
         __syncthreads();
     }
@@ -182,15 +211,10 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     T tau = house_smem<T>(L, vnew, red, &beta);
     // left-apply to X[:, 1:]
     if (tau != T(0)) {
-        for (int c = 1 + tid; c < b; c += nt) {
-            T s = T(0);
-            for (int i = 0; i < L; ++i) s = fma(vnew[i], X[i + c * b], s);
-            p[c] = tau * s;
-        }
-        __syncthreads();
+        cols_dot<T>(L, 1, b, X, ld, vnew, tau, p);
         for (int e = tid; e < L * (b - 1); e += nt) {
             int i = e % L, c = 1 + e / L;
-            X[i + c * b] = fma(-vnew[i], p[c], X[i + c * b]);
+            X[i + c * ld] = fma(-vnew[i], p[c], X[i + c * ld]);
         }
         __syncthreads();
     }
@@ -199,18 +223,12 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     __syncthreads();
     for (int e = tid; e < L * b; e += nt) {
         int i = e % L, c = e / L;
-        band[(size_t)(r + i - (cb + c)) + (size_t)(cb + c) * ldb] = X[i + c * b];
+        band[(size_t)(r + i - (cb + c)) + (size_t)(cb + c) * ldb] = X[i + c * ld];
     }
-    // diagonal block
+    two_sided<T>(L, D, ld, vnew, tau, p, red);
     for (int e = tid; e < L * L; e += nt) {
         int i = e % L, c = e / L;
-        D[i + c * b] = band_get(band, ldb, r + i, r + c);
-    }
-    __syncthreads();
-    two_sided<T>(L, D, b, vnew, tau, p, red);
-    for (int e = tid; e < L * L; e += nt) {
-        int i = e % L, c = e / L;
-        if (i >= c) band[(size_t)(i - c) + (size_t)(r + c) * ldb] = D[i + c * b];
+        if (i >= c) band[(size_t)(i - c) + (size_t)(r + c) * ldb] = D[i + c * ld];
     }
     for (int i = tid; i < b; i += nt) v2[slot * b + i] = (i < L) ? vnew[i] : T(0);
     if (tid == 0) tau2[slot] = tau;
@@ -260,12 +278,12 @@ cudaError_t sb2st(cudaStream_t st, int n, int b, T *band, int ldb, double *d, do
         a.n = n; a.b = b; a.ldb = ldb; a.S = S;
         a.tmax = 3ll * (n - 3) + (S - 1);
         a.count = sync; a.gen = sync + 1; a.status = status;
-        size_t smem = (2 * (size_t)b * b + 3 * b) * sizeof(T);
+        size_t smem = (2 * (size_t)b * (b + 8) + 3 * b) * sizeof(T);
         static bool attr_set[2] = {false, false};
         int ai = sizeof(T) == 8 ? 0 : 1;
         if (!attr_set[ai]) {
             // opt in once for the largest band width (64)
-            const size_t smax = (2 * 64 * 64 + 3 * 64) * sizeof(T);
+            const size_t smax = (2 * 64 * 72 + 3 * 64) * sizeof(T);
             if ((err = cudaFuncSetAttribute(chase_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smax)) != cudaSuccess)
                 return err;
@@ -299,57 +317,110 @@ template cudaError_t sb2st<float>(cudaStream_t, int, int, float *, int, double *
 // ------------------------------------------------------------------ Q2 back-transform
 // Z <- Q2 Z. Q2 = prod over sweep blocks J (ascending) of prod over steps t (descending)
 // of W(J,t) = H(J,t) H(J+1,t) ... H(J+m-1,t); so Z is updated for J descending, t
-// ascending and, inside W(J,t), sweeps descending. Each warp owns a pair of columns of
-// Z and keeps the rows of the current window in a shared-memory ring; the reflectors of
-// one (J, t) are staged once per CTA.
-constexpr int kQ2Cols = 16;     // columns per CTA (2 per warp, 8 warps)
+// ascending and, inside W(J,t), sweeps descending. Every lane owns one column of Z and
+// keeps the rows of the current window in a shared-memory ring (row-major across the
+// CTA's columns, so a warp's accesses are conflict-free); the dot product v^T z of each
+// reflector is lane-local. The reflectors of one (J, t) are staged once per CTA.
 constexpr int kQ2Sweeps = 64;   // m: sweeps per block
-constexpr int kQ2Ring = 256;    // ring rows (>= m + 2b - 1 for b <= 64)
-constexpr int kQ2RingLd = kQ2Ring + 16;  // per-column stride: the two columns of a warp use
-                                         // disjoint shared-memory banks
+constexpr int kQ2Ring = 256;    // ring rows (>= m + 2b - 1 for b <= 64), power of two
+constexpr int kQ2Lanes = 8;     // lanes per column
+constexpr int kQ2RingLd = kQ2Ring + 8;  // column stride of the ring: the 4 columns of a warp
+                                        // start 8 banks apart
+// columns per CTA: binary32 32 (256 threads); binary64 8 (64 threads), so that the
+// n_state columns of the binary64 route still spread over all SMs
+template <typename T> struct Q2Cols;
+template <> struct Q2Cols<float> { static constexpr int v = 32; };
+template <> struct Q2Cols<double> { static constexpr int v = 8; };
+
+__device__ __forceinline__ void cp_async_bytes(void *dst, const void *src, int bytes)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (bytes == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void q2_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void q2_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 template <typename T>
-__global__ void __launch_bounds__(256) apply_q2_kernel(int n, int b, int S, const T *__restrict__ v2,
-                                                        const T *__restrict__ tau2, int k, T *z,
-                                                        int ldz)
+__global__ void __launch_bounds__(256)
+apply_q2_kernel(int n, int b, int S, const T *__restrict__ v2, const T *__restrict__ tau2, int k,
+                T *z, int ldz)
 {
-    extern __shared__ unsigned char smem_raw[];
+    constexpr int kQ2Cols = Q2Cols<T>::v;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *ring = reinterpret_cast<T *>(smem_raw);          // kQ2Cols x kQ2RingLd, [col][slot]
-    T *vs = ring + kQ2RingLd * kQ2Cols;                 // m x b staged reflectors
-    T *ts = vs + kQ2Sweeps * b;                         // m taus
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int col0 = blockIdx.x * kQ2Cols;
-    const int lc = warp * 2 + (lane >> 4);              // local column of this lane
-    const int gc = col0 + lc;
-    const int sub = lane & 15;                          // row lane within the column
-    const bool col_ok = gc < k;
+    T *vsb = ring + kQ2Cols * kQ2RingLd;                // 2 x (m x b) staged reflectors
+    T *tsb = vsb + 2 * kQ2Sweeps * b;                   // 2 x m taus
+    const int tid = threadIdx.x;
+    const int lc = tid / kQ2Lanes;                      // local column
+    const int sub = tid % kQ2Lanes;                     // row lane
+    const int c0 = blockIdx.x * kQ2Cols;
+    const int ncol = min(kQ2Cols, k - c0);
+    const bool col_ok = lc < ncol;
     const int nsweep = n - 2;
     const int nblk = (nsweep + kQ2Sweeps - 1) / kQ2Sweeps;
+    const unsigned gmask = 0xffu << ((tid & 31) & ~7);
+    T *myring = ring + lc * kQ2RingLd;
+
+    // asynchronous copy of rows [r0, r1) of the CTA's columns into the ring
+    auto fetch_rows = [&](int r0, int r1) {
+        const int nr = r1 - r0;
+        for (int e = tid; e < nr * ncol; e += blockDim.x) {
+            int r = r0 + e % nr, c = e / nr;
+            cp_async_bytes(ring + c * kQ2RingLd + (r & (kQ2Ring - 1)), z + (size_t)r + (size_t)(c0 + c) * ldz,
+                           (int)sizeof(T));
+        }
+    };
+    auto store_rows = [&](int r0, int r1) {
+        const int nr = r1 - r0;
+        for (int e = tid; e < nr * ncol; e += blockDim.x) {
+            int r = r0 + e % nr, c = e / nr;
+            z[(size_t)r + (size_t)(c0 + c) * ldz] = ring[c * kQ2RingLd + (r & (kQ2Ring - 1))];
+        }
+    };
+    // asynchronous staging of the reflectors of step t of sweeps [J, Jend) (zeros / tau 0
+    // for sweeps that have no step t)
+    auto fetch_refl = [&](int J, int Jend, int t, int buf) {
+        T *vs = vsb + buf * kQ2Sweeps * b;
+        T *ts = tsb + buf * kQ2Sweeps;
+        for (int e = tid; e < (Jend - J) * b; e += blockDim.x) {
+            int jj = e / b, i = e % b;
+            int j = J + jj;
+            int Sj = (n - 2 - j) / b + 1;
+            if (t < Sj) cp_async_bytes(vs + jj * b + i, v2 + ((size_t)j * S + t) * b + i, (int)sizeof(T));
+            else vs[jj * b + i] = T(0);
+        }
+        for (int jj = tid; jj < Jend - J; jj += blockDim.x) {
+            int j = J + jj;
+            int Sj = (n - 2 - j) / b + 1;
+            if (t < Sj) cp_async_bytes(ts + jj, tau2 + (size_t)j * S + t, (int)sizeof(T));
+            else ts[jj] = T(0);
+        }
+    };
 
     for (int jb = nblk - 1; jb >= 0; --jb) {
         const int J = jb * kQ2Sweeps;
         const int Jend = min(nsweep, J + kQ2Sweeps);  // sweeps J .. Jend-1
         const int SJ = (n - 2 - J) / b + 1;
         int lo = J + 1;                                // window [lo, hi)
-        int hi = min(n, Jend + b);                     // rows of step 0: up to (Jend-1)+1+b-1
-        // initial load
-        for (int r = lo + sub; r < hi; r += 16)
-            ring[lc * kQ2RingLd + (r % kQ2Ring)] = col_ok ? z[(size_t)r + (size_t)gc * ldz] : T(0);
+        int hi = min(n, Jend + b);
+        __syncthreads();
+        fetch_rows(lo, hi);
+        fetch_refl(J, Jend, 0, 0);
+        q2_commit();
         for (int t = 0; t < SJ; ++t) {
-            // stage reflectors (j, t) for j in [J, Jend)
+            const int buf = t & 1;
+            q2_wait_all();
             __syncthreads();
-            for (int e = threadIdx.x; e < (Jend - J) * b; e += blockDim.x) {
-                int jj = e / b, i = e % b;
-                int j = J + jj;
-                int Sj = (n - 2 - j) / b + 1;
-                vs[jj * b + i] = (t < Sj) ? v2[((size_t)j * S + t) * b + i] : T(0);
+            // prefetch what step t+1 needs: its reflectors and the b rows entering the window
+            const int nlo = min(lo + b, n), nhi = min(hi + b, n);
+            if (t + 1 < SJ) {
+                fetch_refl(J, Jend, t + 1, buf ^ 1);
+                fetch_rows(hi, nhi);
             }
-            for (int jj = threadIdx.x; jj < Jend - J; jj += blockDim.x) {
-                int j = J + jj;
-                int Sj = (n - 2 - j) / b + 1;
-                ts[jj] = (t < Sj) ? tau2[(size_t)j * S + t] : T(0);
-            }
-            __syncthreads();
+            q2_commit();
+            const T *vs = vsb + buf * kQ2Sweeps * b;
+            const T *ts = tsb + buf * kQ2Sweeps;
             for (int j = Jend - 1; j >= J; --j) {
                 const int jj = j - J;
                 const T tau = ts[jj];
@@ -357,33 +428,35 @@ __global__ void __launch_bounds__(256) apply_q2_kernel(int n, int b, int S, cons
                 const int r0 = j + 1 + t * b;
                 const int L = min(b, n - r0);
                 if (L <= 0) continue;
-                T s = T(0);
-                for (int i = sub; i < L; i += 16)
-                    s = fma(vs[jj * b + i], ring[lc * kQ2RingLd + ((r0 + i) % kQ2Ring)], s);
-                for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                s *= tau;
-                for (int i = sub; i < L; i += 16) {
-                    T &zr = ring[lc * kQ2RingLd + ((r0 + i) % kQ2Ring)];
-                    zr = fma(-s, vs[jj * b + i], zr);
+                const T *v = vs + jj * b;
+                T sdot = T(0);
+#pragma unroll 8
+                for (int i = sub; i < L; i += kQ2Lanes)
+                    sdot = fma(v[i], myring[(r0 + i) & (kQ2Ring - 1)], sdot);
+                sdot += __shfl_xor_sync(gmask, sdot, 4);
+                sdot += __shfl_xor_sync(gmask, sdot, 2);
+                sdot += __shfl_xor_sync(gmask, sdot, 1);
+                const T sc = tau * sdot;
+#pragma unroll 8
+                for (int i = sub; i < L; i += kQ2Lanes) {
+                    T &zr = myring[(r0 + i) & (kQ2Ring - 1)];
+                    zr = fma(-sc, v[i], zr);
                 }
-                __syncwarp();
+                __syncwarp(gmask);
             }
-            // slide the window by b rows: store [lo, lo+b), load [hi, hi+b)
-            int nlo = min(lo + b, n), nhi = min(hi + b, n);
-            __syncwarp();
-            for (int r = lo + sub; r < nlo; r += 16)
-                if (col_ok) z[(size_t)r + (size_t)gc * ldz] = ring[lc * kQ2RingLd + (r % kQ2Ring)];
-            __syncwarp();
-            for (int r = hi + sub; r < nhi; r += 16)
-                ring[lc * kQ2RingLd + (r % kQ2Ring)] = col_ok ? z[(size_t)r + (size_t)gc * ldz] : T(0);
-            __syncwarp();
-            lo = nlo;
-            hi = nhi;
+            __syncthreads();
+            // rows [lo, nlo) are final for this block of sweeps
+            if (t + 1 < SJ) {
+                store_rows(lo, nlo);
+                lo = nlo;
+                hi = nhi;
+            } else {
+                store_rows(lo, hi);
+            }
+            (void)col_ok;
         }
-        for (int r = lo + sub; r < hi; r += 16)
-            if (col_ok) z[(size_t)r + (size_t)gc * ldz] = ring[lc * kQ2RingLd + (r % kQ2Ring)];
-        __syncwarp();
     }
+    q2_wait_all();
 }
 
 template <typename T>
@@ -394,18 +467,20 @@ cudaError_t apply_q2(cudaStream_t st, int n, int b, const T *v2, const T *tau2, 
     if (n < 3 || k <= 0) return cudaSuccess;
     if (b > 64 || kQ2Sweeps + 2 * b - 1 > kQ2Ring) return cudaErrorInvalidValue;
     const int S = sb2st_steps(n, b);
-    size_t smem = ((size_t)kQ2RingLd * kQ2Cols + (size_t)kQ2Sweeps * b + kQ2Sweeps) * sizeof(T);
+    constexpr int kQ2Cols = Q2Cols<T>::v;
+    size_t smem = ((size_t)kQ2Cols * kQ2RingLd + 2 * (size_t)kQ2Sweeps * b + 2 * kQ2Sweeps) * sizeof(T);
     static bool attr_set[2] = {false, false};
     int ai = sizeof(T) == 8 ? 0 : 1;
     if (!attr_set[ai]) {
-        const size_t smax = ((size_t)kQ2RingLd * kQ2Cols + (size_t)kQ2Sweeps * 64 + kQ2Sweeps) * sizeof(T);
+        const size_t smax =
+            ((size_t)kQ2Cols * kQ2RingLd + 2 * (size_t)kQ2Sweeps * 64 + 2 * kQ2Sweeps) * sizeof(T);
         cudaError_t e = cudaFuncSetAttribute(apply_q2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smax);
         if (e != cudaSuccess) return e;
         attr_set[ai] = true;
     }
     EGB_COUNT_LAUNCH();
-    apply_q2_kernel<T><<<ceil_div(k, kQ2Cols), 256, smem, st>>>(n, b, S, v2, tau2, k, z, ldz);
+    apply_q2_kernel<T><<<ceil_div(k, kQ2Cols), kQ2Cols * kQ2Lanes, smem, st>>>(n, b, S, v2, tau2, k, z, ldz);
     return cudaGetLastError();
 }
 template cudaError_t apply_q2<double>(cudaStream_t, int, int, const double *, const double *, int,
