@@ -131,10 +131,15 @@ __device__ void two_sided(int L, T *D, int ldd, const T *v, T tau, T *p, T *red)
     __syncthreads();
 }
 
+// Loads of data that other CTAs of the same launch write (band, reflectors) bypass L1.
+template <typename T>
+__device__ __forceinline__ T ldg_l2(const T *p) { return __ldcg(p); }
+
 template <typename T>
 __device__ __forceinline__ T band_get(const T *band, int ldb, int r, int c)
 {
-    return (r >= c) ? band[(size_t)(r - c) + (size_t)c * ldb] : band[(size_t)(c - r) + (size_t)r * ldb];
+    return (r >= c) ? ldg_l2(band + (size_t)(r - c) + (size_t)c * ldb)
+                    : ldg_l2(band + (size_t)(c - r) + (size_t)r * ldb);
 }
 
 // One (sweep j, step t) task; all threads of the CTA take part. The b x b tiles use the
@@ -157,7 +162,7 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     if (t == 0) {
         const int L = min(b, n - 1 - j);
         const int r0 = j + 1;
-        for (int i = tid; i < b; i += nt) vnew[i] = (i < L) ? band[(size_t)(1 + i) + (size_t)j * ldb] : T(0);
+        for (int i = tid; i < b; i += nt) vnew[i] = (i < L) ? ldg_l2(band + (size_t)(1 + i) + (size_t)j * ldb) : T(0);
         // D = A[j+1 .. j+L]^2
         for (int e = tid; e < L * L; e += nt) {
             int i = e % L, c = e / L;
@@ -182,12 +187,12 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     const int L = min(b, n - r);
     const int cb = r - b;  // first column of X
     size_t pslot = slot - 1;
-    for (int i = tid; i < b; i += nt) vprev[i] = v2[pslot * b + i];
-    const T taup = tau2[pslot];
+    for (int i = tid; i < b; i += nt) vprev[i] = ldg_l2(v2 + pslot * b + i);
+    const T taup = ldg_l2(tau2 + pslot);
     // X = A[r .. r+L-1, cb .. cb+b-1]  (all strictly below the diagonal, distance 1..2b-1)
     for (int e = tid; e < L * b; e += nt) {
         int i = e % L, c = e / L;
-        X[i + c * ld] = band[(size_t)(r + i - (cb + c)) + (size_t)(cb + c) * ldb];
+        X[i + c * ld] = ldg_l2(band + (size_t)(r + i - (cb + c)) + (size_t)(cb + c) * ldb);
     }
     // D = A[r .. r+L-1]^2 (read now: the task's window is not touched by anyone else)
     for (int e = tid; e < L * L; e += nt) {
@@ -235,27 +240,51 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     __syncthreads();
 }
 
+// Persistent bulge chase with point-to-point ordering: CTA g runs sweeps g, g + G, ... in
+// order; step t of sweep j waits until sweep j-1 has finished step t+2 (or all its steps),
+// which (with the same rule for j-1) orders every pair of overlapping tasks as the
+// sequential algorithm does. progress[j] = number of finished steps of sweep j.
 template <typename T>
-__global__ void __launch_bounds__(256) chase_kernel(T *band, T *v2, T *tau2, ChaseArgs a)
+__global__ void __launch_bounds__(256) chase_kernel(T *band, T *v2, T *tau2, ChaseArgs a, int *progress)
 {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
     __shared__ T red[32];
+    __shared__ int abort_flag;
     const int n = a.n, b = a.b;
     const int nsweep = n - 2;  // sweeps j = 0 .. n-3
-    for (long long time = 0; time <= a.tmax; ++time) {
-        int jhi = (int)min((long long)(nsweep - 1), time / 3);
-        long long lo = (time - (a.S - 1) + 2) / 3;  // ceil((time - (S-1)) / 3)
-        int jlo = (int)max(0ll, lo);
-        for (int j = jlo + blockIdx.x; j <= jhi; j += gridDim.x) {
-            int t = (int)(time - 3ll * j);
-            int Sj = (n - 2 - j) / b + 1;
-            if (t < 0 || t >= Sj) continue;
+    if (threadIdx.x == 0) abort_flag = 0;
+    for (int j = blockIdx.x; j < nsweep; j += gridDim.x) {
+        const int Sj = (n - 2 - j) / b + 1;
+        const int Sprev = (j > 0) ? (n - 2 - (j - 1)) / b + 1 : 0;
+        for (int t = 0; t < Sj; ++t) {
+            if (j > 0) {
+                const int need = min(t + 3, Sprev);
+                if (threadIdx.x == 0) {
+                    volatile int *pv = progress + (j - 1);
+                    volatile int *vst = a.status;
+                    long long it = 0;
+                    while (*pv < need) {
+                        if (vst[ST_CODE] != 0) { abort_flag = 1; break; }
+                        if (++it > kSpinLimit) {
+                            report_error(a.status, ELSI_ERR_TIMEOUT, j);
+                            abort_flag = 1;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    __threadfence();
+                }
+                __syncthreads();
+                if (abort_flag) return;
+            }
             chase_task<T>(a, band, v2, tau2, j, t, smem, red);
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicExch(progress + j, t + 1);
+            }
         }
-        if (!grid_barrier(a.count, a.gen, gridDim.x, a.status)) return;
     }
-    // volatile reads of the band happen in the next kernel (d, e extraction)
 }
 
 template <typename T>
@@ -297,8 +326,9 @@ cudaError_t sb2st(cudaStream_t st, int n, int b, T *band, int ldb, double *d, do
         int G = per_sm * num_sms;
         if (G > maxpar) G = maxpar;
         if (G < 1) G = 1;
-        if ((err = cudaMemsetAsync(sync, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return err;
-        void *args[] = {&band, &v2, &tau2, &a};
+        int *progress = reinterpret_cast<int *>(sync + 64);
+        if ((err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)(n - 2), st)) != cudaSuccess) return err;
+        void *args[] = {&band, &v2, &tau2, &a, &progress};
         EGB_COUNT_LAUNCH();
         if ((err = cudaLaunchCooperativeKernel((void *)chase_kernel<T>, dim3(G), dim3(256), args, smem,
                                                st)) != cudaSuccess)
