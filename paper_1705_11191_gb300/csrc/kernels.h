@@ -90,6 +90,11 @@ cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int 
 template <typename T>
 cudaError_t apply_q2(cudaStream_t st, int n, int b, const T *v2, const T *tau2, int k,
                      T *z, int ldz, int *status);
+// binary32 Z <- Q2 Z with compact-WY groups on the tensor cores (q2wy.cu); tfac: scratch of
+// q2_tfactor_elems(n, b) floats.
+size_t q2_tfactor_elems(int n, int b);
+cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const float *tau2, int k,
+                        float *z, int ldz, float *tfac);
 template <typename T>
 cudaError_t apply_q1(cudaStream_t st, int n, int b, int k, const T *v1, const T *t1, T *z,
                      int ldz, T *work);

@@ -410,7 +410,7 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     CKR(stebz(st, n, w.d, w.e, n, w.w, w.status, 1e-13));
     CKR(stein<float>(st, n, w.d, w.e, n, w.w, X32, n, w.stein, nullptr, w.status));
     CKR(cudaEventRecord(w.ev[STAGE_Q2], st));
-    CKR(apply_q2<float>(st, n, b, V2, TAU2, n, X32, n, w.status));
+    CKR(apply_q2_tc(st, n, b, V2, TAU2, n, X32, n, w.q2f));
     CKR(cudaEventRecord(w.ev[STAGE_Q1], st));
     CKR(apply_q1<float>(st, n, b, n, V1, T1, X32, n, WORK));
     CKR(cudaEventRecord(w.ev[STAGE_BACKSUB], st));

@@ -14,7 +14,7 @@ void free_workspace(elsi_gb_handle_s *h)
 {
     Workspace &w = h->wk;
     void *bufs[] = {w.a, w.l, w.v1, w.edm, w.v2, w.tau2, w.band, w.t1, w.invd, w.work, w.z,
-                    w.d, w.e, w.w, w.f, w.scal, w.stein, w.rf, w.oz, w.ozexp, w.sync, w.status,
+                    w.d, w.e, w.w, w.f, w.scal, w.stein, w.rf, w.oz, w.ozexp, w.q2f, w.sync, w.status,
                     w.host_h, w.host_s, w.host_p};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -69,6 +69,7 @@ static int ensure_workspace(elsi_gb_handle_s *h, int kz)
                                       3 * ozaki_split_elems((int)k, (int)n) +
                                       3 * ozaki_split_elems((int)n, (int)k));
         ENSURE(ozexp, int, 8 * (n + k + 256));
+        ENSURE(q2f, float, q2_tfactor_elems((int)n, b));
     }
     if (!w.status_host && cudaMallocHost((void **)&w.status_host, sizeof(int) * ST_WORDS) != cudaSuccess)
         return set_error(h, ELSI_ERR_NOMEM, "pinned status");

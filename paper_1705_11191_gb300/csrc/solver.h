@@ -42,6 +42,7 @@ struct Workspace {
     EGB_BUF(double, rf)      // refinement buffers
     EGB_BUF(__nv_bfloat16, oz)  // digit planes of the binary64-accurate products
     EGB_BUF(int, ozexp)      // their exponents
+    EGB_BUF(float, q2f)      // compact-WY factors of Q2 (binary32 route)
     EGB_BUF(unsigned, sync)  // grid-barrier words + partial sums
     EGB_BUF(int, status)
     EGB_BUF(double, host_h)  // staging for the _host entry points
