@@ -177,3 +177,65 @@ def config(i: int, tau: float | None = None) -> Problem:
     h, s, lam = build(rng, pos, c["n"], c["per_atom"],
                       tau=1e-2 if tau is None else tau, force_tau=tau is not None)
     return Problem(h, s, c["n_electron"], c["n_state"], c["name"], lam)
+
+
+def kpoint_problem(n: int, kfrac, seed: int, per_atom: int = 15, density: float = 0.01,
+                   tau: float = 1e-2) -> Problem:
+    """Complex Hermitian k-point problem: n basis functions of a periodic cell (a random
+    3D cluster of ceil(n/per_atom) atoms in a cube of side L repeated on a simple cubic
+    lattice), 27 real lattice blocks H_R, O_R (R in {-1, 0, 1}^3) built with the decay
+    rules above on the distances |x_a - x_b - R L|, H_{-R} = H_R^T, and
+        H(k) = sum_R H_R e^{2 pi i kfrac . R},  S(k) = I + alpha sum_R O_R e^{2 pi i kfrac . R}
+    (alpha chosen so that lambda_min(S(k)) >= tau). Draw order: positions, then for
+    R in lexicographic order with R >= -R: u (n x n), g (n x n); then the H_0 diagonal."""
+    rng = np.random.default_rng(seed)
+    n_atoms = math.ceil(n / per_atom)
+    pos = cluster_positions(rng, n_atoms, density=density)
+    side = (n_atoms / density) ** (1.0 / 3.0)
+    atom = basis_atoms(n, per_atom)
+    xyz = pos[atom]
+    kfrac = np.asarray(kfrac, dtype=float)
+    hk = np.zeros((n, n), dtype=np.complex128)
+    ok = np.zeros((n, n), dtype=np.complex128)
+    cells = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
+    done = set()
+    for R in cells:
+        mR = tuple(-x for x in R)
+        if mR in done:
+            continue
+        done.add(R)
+        shift = np.array(R, dtype=float) * side
+        d = np.zeros((n, n))
+        for c in range(3):
+            diff = xyz[:, c][:, None] - (xyz[:, c][None, :] + shift[c])
+            d += diff * diff
+        np.sqrt(d, out=d)
+        u = rng.random((n, n))
+        g = rng.standard_normal((n, n))
+        oR = 0.3 * np.exp(-d / 1.5) * u
+        hR = -0.5 * np.exp(-d / 1.2) * (1.0 + 0.1 * g)
+        if R == (0, 0, 0):
+            # the home cell block is symmetric: mirror the upper triangle, no self term
+            oR = np.triu(oR, 1)
+            oR = oR + oR.T
+            hR = np.triu(hR, 1)
+            hR = hR + hR.T
+            ok += oR
+            hk += hR
+        else:
+            ph = np.exp(2j * np.pi * float(kfrac @ np.array(R, dtype=float)))
+            ok += oR * ph + oR.T * np.conj(ph)
+            hk += hR * ph + hR.T * np.conj(ph)
+    hd = rng.uniform(-1.0, 0.5, n)
+    hk[np.diag_indices(n)] = hd
+    hk = 0.5 * (hk + hk.conj().T)
+    ok = 0.5 * (ok + ok.conj().T)
+    lam = float(np.linalg.eigvalsh(ok)[0]) if n <= 4096 else float(
+        __import__("scipy.sparse.linalg", fromlist=["eigsh"]).eigsh(ok, k=1, which="SA",
+                                                                  return_eigenvectors=False)[0])
+    alpha = 1.0 if 1.0 + lam >= tau else (1.0 - tau) / (-lam)
+    sk = alpha * ok
+    sk[np.diag_indices(n)] = 1.0
+    ne = float(n // 4)
+    return Problem(hk, sk, ne, max(1, int(math.ceil(ne / 2))), f"kpoint-n{n}-seed{seed}",
+                   1.0 + alpha * lam)

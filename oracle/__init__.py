@@ -191,3 +191,41 @@ def solve(h, s, n_state: int, n_el: float, *, unit_ovlp: bool = False,
     if rc == -2:
         raise OracleError("occupation failed")
     return dict(eval=ev, C=c, f=f, mu=mu.value, P=p, W=w, energy=e.value)
+
+
+def embed_hermitian(a):
+    """Real symmetric form [[Re A, -Im A], [Im A, Re A]] of a complex Hermitian A."""
+    a = np.asarray(a, dtype=np.complex128)
+    re, im = a.real, a.imag
+    return np.asfortranarray(np.block([[re, -im], [im, re]]))
+
+
+def solve_complex(h, s, n_state: int, n_el: float, *, unit_ovlp: bool = False,
+                  scheme: int = SCHEME_INTEGER, kt: float = 0.0, occ_accuracy: float = 1e-12,
+                  mu_max_steps: int = 200, want_pw: bool = True):
+    """Complex Hermitian path (sec. 4.4, elsi_ev_complex / elsi_dm_complex): the real
+    symmetric pencil of size 2n has each eigenvalue of (H, S) twice (eigenvectors [x; y]
+    and [-y; x] for c = x + iy). The complex eigenvalue l is real eigenvalue 2l and its
+    eigenvector x + iy comes from real eigenvector 2l. Occupations are computed on the
+    complex eigenvalues and given to both real states of a pair, so that
+    P_emb = sum f v v^T = [[Re P, -Im P], [Im P, Re P]] with P = sum_l f_l c_l c_l^H."""
+    h = np.asarray(h, dtype=np.complex128)
+    n = h.shape[0]
+    he = embed_hermitian(h)
+    se = embed_hermitian(s) if s is not None else None
+    r = solve(he, se, 2 * n_state, 2.0 * n_state, unit_ovlp=unit_ovlp or s is None,
+              want_pw=False)
+    ev = r["eval"][0::2].copy()
+    c2 = r["C"][:, 0::2]
+    out = dict(eval=ev, C=c2[:n] + 1j * c2[n:], P=None, W=None)
+    f, mu = occupation(ev[:n_state], n_el, scheme=scheme, kt=kt, occ_accuracy=occ_accuracy,
+                       mu_max_steps=mu_max_steps)
+    out.update(f=f, mu=mu, energy=float(np.sum(f * ev[:n_state])))
+    if want_pw:
+        f2 = np.repeat(f, 2)
+        e2 = r["eval"][: 2 * n_state]
+        pe = weighted_outer(r["C"], f2)
+        we = weighted_outer(r["C"], f2 * e2)
+        out["P"] = pe[:n, :n] + 1j * pe[n:, :n]
+        out["W"] = we[:n, :n] + 1j * we[n:, :n]
+    return out

@@ -102,8 +102,8 @@ void orc_standard_form(int n, const double *h, const double *l, double *ht)
  *     c = 1/sqrt(1+t^2),  s = t c.
  * The rotations of one round act on disjoint index pairs, so they are all computed
  * from the same A and applied together: A <- J^T A J, V <- V J.
- * A rotation is skipped when a_pq is negligible: |a_pq| <= eps*sqrt(|a_pp a_qq|)
- * (Demmel & Veselic 1992) or |a_pq| <= 1e-18 * ||A||_F.
+ * A rotation is skipped when a_pq is negligible: |a_pq| <= 8 eps sqrt(|a_pp a_qq|)
+ * (the relative criterion of Demmel & Veselic 1992) or |a_pq| <= 2 eps ||A||_F / sqrt(n).
  * Returns the number of sweeps used, or -1 if max_sweeps passed without convergence.
  * ---------------------------------------------------------------------------------- */
 int orc_jacobi(int n, double *a, double *w, double *v, int max_sweeps)
@@ -116,7 +116,14 @@ int orc_jacobi(int n, double *a, double *w, double *v, int max_sweeps)
     double fro = 0.0;
     for (size_t i = 0; i < (size_t)n * (size_t)n; ++i) fro += a[i] * a[i];
     fro = sqrt(fro);
-    const double abs_tol = 1e-18 * fro;
+    /* entries below the rounding level of the whole matrix (a few eps ||A||_F per row)
+     * cannot be reduced by a rotation either; this matters for (near-)zero eigenvalues */
+    const double abs_tol = 2.0 * eps * fro / sqrt((double)n);
+    /* A rotation on a pair whose off-diagonal entry is already at the rounding level of
+     * its diagonal entries cannot reduce it further; with exactly degenerate eigenvalues
+     * (the real form of a complex Hermitian matrix has every eigenvalue twice) such
+     * rotations would repeat forever. The skip rule therefore allows 8 eps. */
+    const double rel_tol = 8.0 * eps;
 
     const int m = (n % 2) ? n + 1 : n; /* tournament size, one dummy player if n odd */
     int *pp = (int *)malloc(sizeof(int) * (size_t)(m / 2));
@@ -138,7 +145,7 @@ int orc_jacobi(int n, double *a, double *w, double *v, int max_sweeps)
                 if (q >= n) continue; /* dummy player */
                 double apq = A_(a, n, p, q);
                 double app = A_(a, n, p, p), aqq = A_(a, n, q, q);
-                if (fabs(apq) <= abs_tol || fabs(apq) <= eps * sqrt(fabs(app * aqq))) continue;
+                if (fabs(apq) <= abs_tol || fabs(apq) <= rel_tol * sqrt(fabs(app * aqq))) continue;
                 double theta = (aqq - app) / (2.0 * apq);
                 double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
                 double c = 1.0 / sqrt(1.0 + t * t);

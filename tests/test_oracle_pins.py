@@ -274,3 +274,53 @@ def test_config0_invariants(cfg0):
     assert abs(np.trace(W @ S) - e) < 1e-9 * abs(e)
     C = r["C"]
     assert np.max(np.abs(C.T @ S @ C - np.eye(C.shape[1]))) < 1e-12
+
+
+# ---------------------------------------------------------------- complex Hermitian path
+def _complex_chain(n, t, phi):
+    h = np.zeros((n, n), dtype=np.complex128)
+    i = np.arange(n - 1)
+    h[i, i + 1] = t * np.exp(1j * phi)
+    h[i + 1, i] = t * np.exp(-1j * phi)
+    return h
+
+
+@pytest.mark.parametrize("n,phi", [(9, 0.3), (24, 1.1)])
+def test_complex_chain_closed_form(n, phi):
+    """H_{j,j+1} = t e^{i phi}: the gauge change c_j -> e^{i j phi} c_j maps it to the real
+    chain, so eps_k = 2 t cos(k pi/(n+1)) for every phase."""
+    t = -0.6
+    r = oracle.solve_complex(_complex_chain(n, t, phi), None, n, float(n), unit_ovlp=True)
+    exact = np.sort(2 * t * np.cos(np.arange(1, n + 1) * np.pi / (n + 1)))
+    np.testing.assert_allclose(r["eval"], exact, rtol=0, atol=1e-13)
+    C = r["C"]
+    np.testing.assert_allclose(C.conj().T @ C, np.eye(n), atol=1e-12)
+
+
+@pytest.mark.parametrize("n,seed", [(12, 1), (45, 2)])
+def test_complex_random_vs_lapack(n, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    h = a + a.conj().T
+    b = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    s = b @ b.conj().T / n + np.eye(n)
+    k = n // 2
+    r = oracle.solve_complex(h, s, k, float(k))
+    w, v = sla.eigh(h, s)
+    np.testing.assert_allclose(r["eval"], w, rtol=0, atol=1e-11 * max(1, np.abs(w).max()))
+    f = r["f"]
+    p_ref = (v[:, :k] * f) @ v[:, :k].conj().T
+    np.testing.assert_allclose(r["P"], p_ref, atol=1e-11)
+    C = r["C"]
+    np.testing.assert_allclose(C.conj().T @ s @ C, np.eye(k), atol=1e-11)
+
+
+def test_complex_kpoint_invariants():
+    p = ksinputs.kpoint_problem(75, (0.25, 0.5, 0.0), seed=3)
+    r = oracle.solve_complex(p.h, p.s, p.n_state, p.n_electron)
+    P, S, H, W = r["P"], p.s, p.h, r["W"]
+    assert abs(np.trace(P @ S).real - p.n_electron) < 1e-10
+    np.testing.assert_allclose(P, P.conj().T, atol=1e-13)
+    e = r["energy"]
+    assert abs(np.trace(P @ H).real - e) < 1e-10 * abs(e)
+    assert abs(np.trace(W @ S).real - e) < 1e-10 * abs(e)
