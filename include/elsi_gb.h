@@ -101,6 +101,20 @@ int elsi_ev_real(elsi_handle h, double *ham, const double *ovlp, double *eval, d
 int elsi_dm_real(elsi_handle h, double *ham, const double *ovlp, double *den_mat,
                  double *energy);
 
+/* elsi_ev_complex / elsi_dm_complex (sec. 4.4: "same as elsi_ev_real, except that the
+ * Hamiltonian matrix, overlap matrix and eigenvectors are complex-valued"). ham, ovlp,
+ * evec, den_mat are complex Hermitian arrays stored as interleaved (re, im) binary64 pairs,
+ * column-major (2 * n_basis * n_basis doubles; evec 2 * n_basis * n_state doubles);
+ * eval has n_basis real entries, ascending. The problem is solved as the real symmetric
+ * pencil [[Re H, -Im H], [Im H, Re H]] of size 2 n_basis, which has each eigenvalue twice;
+ * P = sum_l f_l c_l c_l^H, E = sum_l f_l eps_l. Inputs are not modified. */
+int elsi_ev_complex(elsi_handle h, const double *ham, const double *ovlp, double *eval,
+                    double *evec);
+int elsi_dm_complex(elsi_handle h, const double *ham, const double *ovlp, double *den_mat,
+                    double *energy);
+/* W = sum_l f_l eps_l c_l c_l^H of the last elsi_dm_complex call (interleaved). */
+int elsi_get_edm_complex(elsi_handle h, double *edm);
+
 /* Energy-weighted density matrix W = sum_l f_l eps_l c_l c_l^T of the last
  * elsi_dm_real call (the paper names it only as a PEXSI output, sec. 4.4). */
 int elsi_get_edm_real(elsi_handle h, double *edm);

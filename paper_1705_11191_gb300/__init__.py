@@ -60,6 +60,9 @@ def _declare(lib):
         "elsi_ev_real": ([H, _vp, _vp, _vp, _vp], i),
         "elsi_dm_real": ([H, _vp, _vp, _vp, _dp], i),
         "elsi_get_edm_real": ([H, _vp], i),
+        "elsi_ev_complex": ([H, _vp, _vp, _vp, _vp], i),
+        "elsi_dm_complex": ([H, _vp, _vp, _vp, _dp], i),
+        "elsi_get_edm_complex": ([H, _vp], i),
         "elsi_get_mu": ([H, _dp], i),
         "elsi_get_occ": ([H, _vp], i),
         "elsi_dm_real_host": ([H, _vp, _vp, _vp, _vp, _dp], i),
@@ -112,13 +115,20 @@ def stage_names() -> list[str]:
 STAGES = None
 
 
-def _ptr(t) -> int:
+def _ptr(t, dtype=None) -> int:
     import torch
+    dtype = dtype or torch.float64
     if not isinstance(t, torch.Tensor):
         raise TypeError("expected a torch tensor")
-    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
-        raise ValueError("expected a contiguous float64 CUDA tensor")
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous {dtype} CUDA tensor")
     return t.data_ptr()
+
+
+def _colmajor(t):
+    """Column-major copy of a (n, n) tensor (the library's layout); a no-op copy is
+    avoided for real symmetric inputs by the callers."""
+    return t.transpose(0, 1).contiguous()
 
 
 class Handle:
@@ -215,6 +225,41 @@ class Handle:
                                     _vp(_ptr(p)), ctypes.byref(e))
         self._check(rc, "elsi_dm_real")
         return p, e.value
+
+    def ev_complex(self, ham, ovlp=None):
+        """Complex Hermitian eigenpairs: (eval (n,) float64, evec (n, n_state) complex128)."""
+        import torch
+        c128 = torch.complex128
+        hc = _colmajor(ham)
+        sc = _colmajor(ovlp) if ovlp is not None else None
+        ev = torch.empty(self.n, dtype=torch.float64, device=ham.device)
+        vec = torch.empty((self.n_state, self.n), dtype=c128, device=ham.device)
+        rc = self._lib.elsi_ev_complex(self._h, _vp(_ptr(hc, c128)),
+                                       _vp(_ptr(sc, c128) if sc is not None else None),
+                                       _vp(_ptr(ev)), _vp(_ptr(vec, c128)))
+        self._check(rc, "elsi_ev_complex")
+        return ev, vec.t()
+
+    def dm_complex(self, ham, ovlp=None):
+        """Complex density matrix P (n, n) complex128 and the band energy."""
+        import torch
+        c128 = torch.complex128
+        hc = _colmajor(ham)
+        sc = _colmajor(ovlp) if ovlp is not None else None
+        p = torch.empty((self.n, self.n), dtype=c128, device=ham.device)
+        e = ctypes.c_double(0.0)
+        rc = self._lib.elsi_dm_complex(self._h, _vp(_ptr(hc, c128)),
+                                       _vp(_ptr(sc, c128) if sc is not None else None),
+                                       _vp(_ptr(p, c128)), ctypes.byref(e))
+        self._check(rc, "elsi_dm_complex")
+        return p.t(), e.value
+
+    def get_edm_complex(self):
+        import torch
+        w = torch.empty((self.n, self.n), dtype=torch.complex128, device="cuda")
+        self._check(self._lib.elsi_get_edm_complex(self._h, _vp(_ptr(w, torch.complex128))),
+                    "elsi_get_edm_complex")
+        return w.t()
 
     def get_edm(self, out=None):
         import torch

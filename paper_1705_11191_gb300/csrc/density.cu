@@ -15,75 +15,84 @@ __device__ __forceinline__ double occ_phi(int scheme, double x)
 
 // One CTA. Spin factor g = 2. scheme 0: aufbau filling; 1/2: bisection on mu with the
 // exact-charge correction of sec. 4.4 when occ_accuracy is not reached.
-__global__ void occupation_kernel(int k, const double *eps, double n_el, int scheme, double kt,
-                                  double occ_accuracy, int mu_max_steps, double *f, double *out,
-                                  int *status)
+// stride 2 ("pairs"): states 2i and 2i+1 are the two real forms of one complex state;
+// occupations are computed on eps[2i] with n_el / 2 electrons and given to both, and the
+// reported energy is the sum over all real states (twice the complex band energy).
+__global__ void occupation_kernel(int k, const double *eps_all, double n_el_all, int scheme,
+                                  double kt, double occ_accuracy, int mu_max_steps, double *f,
+                                  double *out, int *status, int stride)
 {
     __shared__ double red[32];
-    __shared__ double s_lo, s_hi;
-    __shared__ int s_done;
     const double g = 2.0;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int kk = k / stride;
+    const double n_el = n_el_all / stride;
+    auto eps = [&](int l) { return eps_all[(size_t)l * stride]; };
     if (scheme == ELSI_OCC_INTEGER) {
         double es = 0.0;
-        for (int l = tid; l < k; l += nt) {
+        for (int l = tid; l < kk; l += nt) {
             double fl = fmin(g, fmax(0.0, n_el - g * l));
-            f[l] = fl;
-            es += fl * eps[l];
+            f[(size_t)l * stride] = fl;
+            es += fl * eps(l);
         }
         es = block_sum(es, red);
         if (tid == 0) {
             int top = (int)ceil(n_el / g) - 1;
             if (top < 0) top = 0;
-            if (top > k - 1) top = k - 1;
-            out[0] = eps[top];
-            out[1] = es;
+            if (top > kk - 1) top = kk - 1;
+            out[0] = eps(top);
+            out[1] = stride * es;
         }
-        return;
-    }
-    auto count = [&](double mu) {
-        double s = 0.0;
-        for (int l = tid; l < k; l += nt) s += g * occ_phi(scheme, (eps[l] - mu) / kt);
-        return block_sum(s, red);
-    };
-    double lo = eps[0], hi = eps[k - 1];
-    for (int it = 0; it < 1000 && count(lo) > n_el; ++it) lo -= 1.0;
-    for (int it = 0; it < 1000 && count(hi) < n_el; ++it) hi += 1.0;
-    double mu = hi;
-    int converged = 0;
-    for (int step = 0; step < mu_max_steps; ++step) {
-        double mid = 0.5 * (lo + hi);
-        double nm = count(mid);
-        if (fabs(nm - n_el) <= occ_accuracy) { mu = mid; converged = 1; break; }
-        if (nm < n_el) lo = mid; else hi = mid;
-    }
-    if (!converged) mu = hi;
-    for (int l = tid; l < k; l += nt) f[l] = g * occ_phi(scheme, (eps[l] - mu) / kt);
-    __syncthreads();
-    if (!converged && tid == 0) {
-        double surplus = -n_el;
-        for (int l = 0; l < k; ++l) surplus += f[l];
-        for (int l = k - 1; l >= 0 && surplus > 0.0; --l) {
-            double take = f[l] < surplus ? f[l] : surplus;
-            f[l] -= take;
-            surplus -= take;
+    } else {
+        auto count = [&](double mu) {
+            double s2 = 0.0;
+            for (int l = tid; l < kk; l += nt) s2 += g * occ_phi(scheme, (eps(l) - mu) / kt);
+            return block_sum(s2, red);
+        };
+        double lo = eps(0), hi = eps(kk - 1);
+        for (int it = 0; it < 1000 && count(lo) > n_el; ++it) lo -= 1.0;
+        for (int it = 0; it < 1000 && count(hi) < n_el; ++it) hi += 1.0;
+        double mu = hi;
+        int converged = 0;
+        for (int step = 0; step < mu_max_steps; ++step) {
+            double mid = 0.5 * (lo + hi);
+            double nm = count(mid);
+            if (fabs(nm - n_el) <= occ_accuracy / stride) { mu = mid; converged = 1; break; }
+            if (nm < n_el) lo = mid; else hi = mid;
         }
+        if (!converged) mu = hi;
+        for (int l = tid; l < kk; l += nt) f[(size_t)l * stride] = g * occ_phi(scheme, (eps(l) - mu) / kt);
+        __syncthreads();
+        if (!converged && tid == 0) {
+            double surplus = -n_el;
+            for (int l = 0; l < kk; ++l) surplus += f[(size_t)l * stride];
+            for (int l = kk - 1; l >= 0 && surplus > 0.0; --l) {
+                double fl = f[(size_t)l * stride];
+                double take = fl < surplus ? fl : surplus;
+                f[(size_t)l * stride] = fl - take;
+                surplus -= take;
+            }
+        }
+        __syncthreads();
+        double es = 0.0;
+        for (int l = tid; l < kk; l += nt) es += f[(size_t)l * stride] * eps(l);
+        es = block_sum(es, red);
+        if (tid == 0) { out[0] = mu; out[1] = stride * es; }
     }
     __syncthreads();
-    double es = 0.0;
-    for (int l = tid; l < k; l += nt) es += f[l] * eps[l];
-    es = block_sum(es, red);
-    if (tid == 0) { out[0] = mu; out[1] = es; }
-    (void)s_lo; (void)s_hi; (void)s_done; (void)status;
+    if (stride > 1)
+        for (int l = tid; l < kk; l += nt)
+            for (int q = 1; q < stride; ++q) f[(size_t)l * stride + q] = f[(size_t)l * stride];
+    (void)status;
 }
 
 cudaError_t occupation(cudaStream_t st, int k, const double *eps, double n_el, int scheme,
                        double kt, double occ_accuracy, int mu_max_steps, double *f, double *out,
-                       int *status)
+                       int *status, int stride)
 {
     EGB_COUNT_LAUNCH();
     occupation_kernel<<<1, 1024, 0, st>>>(k, eps, n_el, scheme, kt, occ_accuracy, mu_max_steps, f,
-                                          out, status);
+                                          out, status, stride);
     return cudaGetLastError();
 }
 

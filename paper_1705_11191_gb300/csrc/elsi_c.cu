@@ -85,6 +85,7 @@ int elsi_finalize(elsi_handle *hp)
 {
     if (!hp || check_handle(*hp)) return ELSI_ERR_STATE;
     elsi_gb_handle_s *h = *hp;
+    free_complex(h);
     free_workspace(h);
     h->magic = 0;
     delete h;
@@ -193,6 +194,30 @@ int elsi_dm_real(elsi_handle h, double *ham, const double *ovlp, double *den_mat
     int rc = run_solve(h, rq);
     if (rc == ELSI_OK && energy) *energy = h->energy;
     return rc;
+}
+
+int elsi_ev_complex(elsi_handle h, const double *ham, const double *ovlp, double *eval, double *evec)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!ham || !eval || !evec || (!ovlp && !h->overlap_is_unit))
+        return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    return solve_complex(h, ham, h->overlap_is_unit ? nullptr : ovlp, eval, evec, nullptr, nullptr);
+}
+
+int elsi_dm_complex(elsi_handle h, const double *ham, const double *ovlp, double *den_mat,
+                    double *energy)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!ham || !den_mat || (!ovlp && !h->overlap_is_unit))
+        return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    return solve_complex(h, ham, h->overlap_is_unit ? nullptr : ovlp, nullptr, nullptr, den_mat, energy);
+}
+
+int elsi_get_edm_complex(elsi_handle h, double *edm)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!edm) return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    return get_edm_complex(h, edm);
 }
 
 int elsi_get_edm_real(elsi_handle h, double *edm)

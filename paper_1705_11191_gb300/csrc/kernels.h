@@ -77,9 +77,10 @@ cudaError_t extract_band(cudaStream_t st, int n, int b, const T *a, int lda, T *
 // Eigenvalues il..iu-1 (0-based, ascending) of the symmetric tridiagonal (d, e) by
 // Sturm bisection (w needs count + 4 entries: the Gershgorin bounds follow the values),
 // then eigenvectors of the first kvec of them into z (n x kvec, ldz) as type T.
-// scratch: 2*n*kvec + 8 doubles.
+// scratch: 2*n*kvec + kvec + 16 doubles.
 // tol_rel: stop when the bracket is narrower than tol_rel * ||T|| (0: full binary64).
-cudaError_t stebz(cudaStream_t st, int n, const double *d, const double *e, int count,
+// Off-diagonals of e below 2 eps ||T|| are set to zero first (T splits into blocks).
+cudaError_t stebz(cudaStream_t st, int n, const double *d, double *e, int count,
                   double *w, int *status, double tol_rel = 0.0);
 template <typename T>
 cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int kvec,
@@ -100,9 +101,10 @@ cudaError_t apply_q1(cudaStream_t st, int n, int b, int k, const T *v1, const T 
                      int ldz, T *work);
 
 // ---- occupation, density matrices ----
+// stride 2: consecutive pairs of states are one complex state (see density.cu).
 cudaError_t occupation(cudaStream_t st, int k, const double *eps, double n_el, int scheme,
                        double kt, double occ_accuracy, int mu_max_steps, double *f,
-                       double *out /* [0]=mu [1]=energy */, int *status);
+                       double *out /* [0]=mu [1]=energy */, int *status, int stride = 1);
 // P = C diag(f) C^T and W = C diag(f eps) C^T (lower + mirror); cw: n x k scratch.
 template <typename T>
 cudaError_t density_pw(cudaStream_t st, int n, int k, const T *c, int ldc, const double *f,

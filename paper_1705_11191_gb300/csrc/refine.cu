@@ -532,11 +532,11 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
         CKR(cudaEventRecord(w.ev[STAGE_DENSITY], st));
     } else {
         CKR(occupation(st, k, w.w, h->n_electron, h->scheme, h->kt, h->occ_accuracy,
-                       h->mu_max_steps, w.f, w.scal, w.status));
+                       h->mu_max_steps, w.f, w.scal, w.status, h->occ_stride));
         CKR(cudaEventRecord(w.ev[STAGE_DENSITY], st));
         int kocc = k;
         if (h->scheme == ELSI_OCC_INTEGER) {
-            kocc = (int)((h->n_electron + 1.999999999) / 2.0);
+            kocc = (int)((h->n_electron / h->occ_stride + 1.999999999) / 2.0) * h->occ_stride;
             if (kocc > k) kocc = k;
             if (kocc < 1) kocc = 1;
         }

@@ -57,7 +57,7 @@ static int ensure_workspace(elsi_gb_handle_s *h, int kz)
     ENSURE(w, double, n + 8);
     ENSURE(f, double, n + 8);
     ENSURE(scal, double, 64);
-    ENSURE(stein, double, 2 * n * kz + 16);
+    ENSURE(stein, double, 2 * n * kz + kz + 64);
     ENSURE(sync, unsigned, 64 + 2 * (1024 + 64 + 1024 * 64 + 1024 * 64 * 64));
     ENSURE(status, int, ST_WORDS);
     if (h->precision == ELSI_PREC_FP32_REFINE) {
@@ -165,12 +165,12 @@ static int solve_fp64(elsi_gb_handle_s *h, const SolveRequest &rq)
     } else {
         // ---- sec. 4.4: mu, occupations, band energy
         CK(occupation(st, k, w.w, h->n_electron, h->scheme, h->kt, h->occ_accuracy, h->mu_max_steps,
-                      w.f, w.scal, w.status));
+                      w.f, w.scal, w.status, h->occ_stride));
         CK(cudaEventRecord(w.ev[STAGE_DENSITY], st));
         // ---- Eq. 7: P and W (only columns with possibly nonzero f)
         int kocc = k;
         if (h->scheme == ELSI_OCC_INTEGER) {
-            kocc = (int)((h->n_electron + 1.999999999) / 2.0);
+            kocc = (int)((h->n_electron / h->occ_stride + 1.999999999) / 2.0) * h->occ_stride;
             if (kocc > k) kocc = k;
             if (kocc < 1) kocc = 1;
         }

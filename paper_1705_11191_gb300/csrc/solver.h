@@ -48,6 +48,7 @@ struct Workspace {
     EGB_BUF(double, host_h)  // staging for the _host entry points
     EGB_BUF(double, host_s)
     EGB_BUF(double, host_p)
+    EGB_BUF(double, rfc)     // complex route: real eigenpair staging
 #undef EGB_BUF
     int *status_host = nullptr;  // pinned
     double *scal_host = nullptr; // pinned
@@ -72,6 +73,7 @@ struct elsi_gb_handle_s {
     int refine_max_iter = 3;
     bool reuse_l = false;
     cudaStream_t stream = nullptr;
+    int occ_stride = 1;  // 2 in the real form of a complex problem (pairs of states)
     // state
     bool have_l = false;
     int have_l_prec = -1;
@@ -82,6 +84,9 @@ struct elsi_gb_handle_s {
     float stage_ms[egb::kNumStages] = {};
     std::string last_error;
     egb::Workspace wk;
+    // complex Hermitian problems are solved as real ones of size 2n in this sub-handle
+    elsi_gb_handle_s *cplx = nullptr;
+    bool have_cedm = false;
 };
 
 namespace egb {
@@ -99,5 +104,9 @@ int set_error(elsi_gb_handle_s *h, int code, const char *fmt, ...);
 bool ensure_buf(void **p, size_t *cap, size_t bytes);
 int run_solve(elsi_gb_handle_s *h, const SolveRequest &rq);
 void free_workspace(elsi_gb_handle_s *h);
+int solve_complex(elsi_gb_handle_s *h, const double *ham, const double *ovlp, double *eval,
+                  double *evec, double *den_mat, double *energy);
+int get_edm_complex(elsi_gb_handle_s *h, double *edm);
+void free_complex(elsi_gb_handle_s *h);
 
 }  // namespace egb

@@ -146,7 +146,18 @@ __global__ void bisect_kernel(int n, const double *d, const double *e, int count
     }
 }
 
-cudaError_t stebz(cudaStream_t st, int n, const double *d, const double *e, int count,
+// Off-diagonals below 2 eps ||T|| are set to zero: T splits into unreduced blocks, which
+// changes no eigenvalue by more than 2 eps ||T|| and lets exactly degenerate eigenvalues
+// (e.g. those of a complex Hermitian matrix written as a real one) be found in
+// different blocks.
+__global__ void split_kernel(int n, double *e, const double *bounds)
+{
+    const double tn = bounds[3];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n - 1; i += gridDim.x * blockDim.x)
+        if (fabs(e[i]) <= 2.0 * DBL_EPSILON * tn) e[i] = 0.0;
+}
+
+cudaError_t stebz(cudaStream_t st, int n, const double *d, double *e, int count,
                   double *w, int *status, double tol_rel)
 {
     (void)status;
@@ -155,6 +166,8 @@ cudaError_t stebz(cudaStream_t st, int n, const double *d, const double *e, int 
     double *bounds = w + count;
     EGB_COUNT_LAUNCH();
     gershgorin_kernel<<<1, 1024, 0, st>>>(n, d, e, bounds);
+    EGB_COUNT_LAUNCH();
+    split_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, e, bounds);
     // enough threads to cover the latency: multisection when there are few eigenvalues
     if (count <= 4096) {
         EGB_COUNT_LAUNCH();
@@ -166,29 +179,71 @@ cudaError_t stebz(cudaStream_t st, int n, const double *d, const double *e, int 
     return cudaGetLastError();
 }
 
+// Block of each eigenvalue: with [lo, hi] a small interval around w[l], the eigenvalues of
+// T in it are numbered by block order; w[l] is the (l - count(lo))-th of them. blk[2l],
+// blk[2l+1] = [start, end) of its block.
+__global__ void block_assign_kernel(int n, const double *d, const double *e, int kvec,
+                                    const double *w, const double *bounds, int *blk)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= kvec) return;
+    const double tn = bounds[3], pivmin = bounds[2];
+    const double delta = 8.0 * DBL_EPSILON * fmax(fabs(w[l]), tn) + 4.0 * pivmin;
+    const double lo = w[l] - delta, hi = w[l] + delta;
+    const int clo = sturm_count(n, d, e, lo, pivmin);
+    int r = l - clo;  // rank among the eigenvalues in [lo, hi]
+    if (r < 0) r = 0;
+    double qlo = 1.0, qhi = 1.0;
+    int cl = 0, ch = 0, start = 0;
+    int bs = 0, be = n;
+    for (int i = 0; i < n; ++i) {
+        const double ei2 = (i > 0) ? e[i - 1] * e[i - 1] : 0.0;
+        if (i == 0 || e[i - 1] == 0.0) {
+            qlo = d[i] - lo;
+            qhi = d[i] - hi;
+        } else {
+            qlo = d[i] - lo - ei2 / qlo;
+            qhi = d[i] - hi - ei2 / qhi;
+        }
+        if (fabs(qlo) < pivmin) qlo = -pivmin;
+        if (fabs(qhi) < pivmin) qhi = -pivmin;
+        cl += qlo < 0.0;
+        ch += qhi < 0.0;
+        const bool block_end = (i == n - 1) || (e[i] == 0.0);
+        if (block_end) {
+            if (ch - cl > r) { bs = start; be = i + 1; break; }
+            start = i + 1;
+        }
+    }
+    blk[2 * l] = bs;
+    blk[2 * l + 1] = be;
+}
+
 // Twisted factorisation eigenvector for each of the first kvec eigenvalues.
 template <typename T>
 __global__ void twisted_kernel(int n, const double *__restrict__ d, const double *__restrict__ e,
                                int kvec, const double *__restrict__ w, const double *bounds,
-                               T *z, int ldz, double *dplus, double *uminus, int *status)
+                               const int *__restrict__ blk, T *z, int ldz, double *dplus,
+                               double *uminus, int *status)
 {
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= kvec) return;
     const double lam = w[l];
     const double pivmin = bounds[2];
-    // forward: T - lam I = L+ D+ L+^T
-    double dp = guard_pivot(d[0] - lam, pivmin);
-    dplus[l] = dp;
-    for (int i = 0; i < n - 1; ++i) {
+    const int bs = blk[2 * l], be = blk[2 * l + 1];  // the eigenvalue's block [bs, be)
+    // forward: T_b - lam I = L+ D+ L+^T
+    double dp = guard_pivot(d[bs] - lam, pivmin);
+    dplus[(size_t)bs * kvec + l] = dp;
+    for (int i = bs; i < be - 1; ++i) {
         double lp = e[i] / dp;
         dp = guard_pivot(d[i + 1] - lam - lp * e[i], pivmin);
         dplus[(size_t)(i + 1) * kvec + l] = dp;
     }
-    // backward: T - lam I = U- D- U-^T, twist index r = argmin |gamma_r|
-    double dm = guard_pivot(d[n - 1] - lam, pivmin);
-    double best = fabs(dplus[(size_t)(n - 1) * kvec + l] + dm - (d[n - 1] - lam));
-    int r = n - 1;
-    for (int i = n - 2; i >= 0; --i) {
+    // backward: T_b - lam I = U- D- U-^T, twist index r = argmin |gamma_r|
+    double dm = guard_pivot(d[be - 1] - lam, pivmin);
+    double best = fabs(dplus[(size_t)(be - 1) * kvec + l] + dm - (d[be - 1] - lam));
+    int r = be - 1;
+    for (int i = be - 2; i >= bs; --i) {
         double um = e[i] / dm;
         uminus[(size_t)i * kvec + l] = um;
         dm = guard_pivot(d[i] - lam - um * e[i], pivmin);
@@ -197,27 +252,29 @@ __global__ void twisted_kernel(int n, const double *__restrict__ d, const double
     }
     // pass 1: norm of z (z_r = 1)
     double nrm2 = 1.0, zi = 1.0;
-    for (int i = r - 1; i >= 0; --i) {
+    for (int i = r - 1; i >= bs; --i) {
         zi = -(e[i] / dplus[(size_t)i * kvec + l]) * zi;
         nrm2 += zi * zi;
     }
     zi = 1.0;
-    for (int i = r; i < n - 1; ++i) {
+    for (int i = r; i < be - 1; ++i) {
         zi = -uminus[(size_t)i * kvec + l] * zi;
         nrm2 += zi * zi;
     }
     if (!(nrm2 < DBL_MAX)) { report_error(status, ELSI_ERR_NO_CONVERGENCE, l); nrm2 = 1.0; }
     double s = 1.0 / sqrt(nrm2);
-    // pass 2: write z / ||z||
+    // pass 2: write z / ||z|| (zero outside the block)
     T *zc = z + (size_t)l * ldz;
+    for (int i = 0; i < bs; ++i) zc[i] = T(0);
+    for (int i = be; i < n; ++i) zc[i] = T(0);
     zc[r] = (T)s;
     zi = 1.0;
-    for (int i = r - 1; i >= 0; --i) {
+    for (int i = r - 1; i >= bs; --i) {
         zi = -(e[i] / dplus[(size_t)i * kvec + l]) * zi;
         zc[i] = (T)(zi * s);
     }
     zi = 1.0;
-    for (int i = r; i < n - 1; ++i) {
+    for (int i = r; i < be - 1; ++i) {
         zi = -uminus[(size_t)i * kvec + l] * zi;
         zc[i + 1] = (T)(zi * s);
     }
@@ -268,10 +325,13 @@ cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int 
     (void)cluster_ws;
     if (n <= 0 || kvec <= 0) return cudaSuccess;
     double *bounds = scratch + (size_t)2 * n * kvec;
+    int *blk = reinterpret_cast<int *>(bounds + 8);  // 2 * kvec ints
     EGB_COUNT_LAUNCH();
     gershgorin_kernel<<<1, 1024, 0, st>>>(n, d, e, bounds);
     EGB_COUNT_LAUNCH();
-    twisted_kernel<T><<<ceil_div(kvec, 64), 64, 0, st>>>(n, d, e, kvec, w, bounds, z, ldz, scratch,
+    block_assign_kernel<<<ceil_div(kvec, 64), 64, 0, st>>>(n, d, e, kvec, w, bounds, blk);
+    EGB_COUNT_LAUNCH();
+    twisted_kernel<T><<<ceil_div(kvec, 64), 64, 0, st>>>(n, d, e, kvec, w, bounds, blk, z, ldz, scratch,
                                                         scratch + (size_t)n * kvec, status);
     EGB_COUNT_LAUNCH();
     cluster_orth_kernel<T><<<kvec, 256, 0, st>>>(n, kvec, w, bounds, 1e-5, z, ldz, status);
