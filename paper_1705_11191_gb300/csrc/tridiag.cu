@@ -280,11 +280,45 @@ __global__ void twisted_kernel(int n, const double *__restrict__ d, const double
     }
 }
 
-// One CTA per cluster start: Gram-Schmidt (two passes) within clusters of eigenvalues
-// closer than tol_rel * ||T||.
+// Gram-Schmidt of vector zv against the cluster vectors i0 .. v-1 (two passes); returns
+// the squared norm left.
 template <typename T>
-__global__ void cluster_orth_kernel(int n, int kvec, const double *w, const double *bounds,
-                                    double tol_rel, T *z, int ldz, int *status)
+__device__ double cluster_project(int n, int i0, int v, T *z, int ldz, double *red)
+{
+    T *zv = z + (size_t)v * ldz;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int u = i0; u < v; ++u) {
+            const T *zu = z + (size_t)u * ldz;
+            double s = 0.0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)zu[i] * (double)zv[i];
+            s = block_sum(s, red);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) zv[i] = (T)((double)zv[i] - s * (double)zu[i]);
+            __syncthreads();
+        }
+    }
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)zv[i] * (double)zv[i];
+    return block_sum(s, red);
+}
+
+__device__ __forceinline__ double hash_unit(unsigned a, unsigned b)
+{
+    unsigned h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
+    h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+    return (double)h * (2.0 / 4294967296.0) - 1.0;
+}
+
+// One CTA per cluster start: Gram-Schmidt (two passes) within clusters of eigenvalues
+// closer than tol_rel * ||T||. A vector that the projection nearly annihilates (its
+// eigenvalue coincides with an earlier one to working accuracy, as for the pairs of the
+// real form of a complex Hermitian matrix) is replaced by one step of inverse iteration
+// on its block, x = (T_b - lambda I)^{-1} b for a pseudo-random b, using the L+ D+ L+^T
+// factors that the twisted factorisation left in dplus (the vector's spent U- column
+// holds the intermediate values), and is then projected and normalised again.
+template <typename T>
+__global__ void cluster_orth_kernel(int n, int kvec, const double *w, const double *e,
+                                    const double *bounds, const int *blk, double tol_rel,
+                                    const double *dplus, double *work, T *z, int ldz, int *status)
 {
     __shared__ double red[32];
     const int i0 = blockIdx.x;
@@ -295,24 +329,55 @@ __global__ void cluster_orth_kernel(int n, int kvec, const double *w, const doub
     if (i1 - i0 < 2) return;
     for (int v = i0 + 1; v < i1; ++v) {
         T *zv = z + (size_t)v * ldz;
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int u = i0; u < v; ++u) {
-                const T *zu = z + (size_t)u * ldz;
-                double s = 0.0;
-                for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)zu[i] * (double)zv[i];
-                s = block_sum(s, red);
-                for (int i = threadIdx.x; i < n; i += blockDim.x) zv[i] = (T)((double)zv[i] - s * (double)zu[i]);
-                __syncthreads();
+        double s = cluster_project(n, i0, v, z, ldz, red);
+        for (int attempt = 0; attempt < 3 && s < 1e-4; ++attempt) {
+            if (threadIdx.x == 0) {
+                const int bs = blk[2 * v], be = blk[2 * v + 1];
+                double *x = work + v;  // x[i * kvec]
+                // forward: L+ y = b; backward: L+^T x = D+^{-1} y. Entries are rescaled
+                // (all at once) whenever one exceeds 2^500.
+                const double big = 0x1p500, shrink = 0x1p-500;
+                double y = 0.0;
+                for (int i = bs; i < be; ++i) {
+                    const double bi = hash_unit((unsigned)(v * 7919 + attempt), (unsigned)i);
+                    y = (i == bs) ? bi : bi - (e[i - 1] / dplus[(size_t)(i - 1) * kvec + v]) * y;
+                    if (fabs(y) > big) {
+                        for (int j = bs; j < i; ++j) x[(size_t)j * kvec] *= shrink;
+                        y *= shrink;
+                    }
+                    x[(size_t)i * kvec] = y;
+                }
+                double xi = 0.0;
+                for (int i = be - 1; i >= bs; --i) {
+                    const double yi = x[(size_t)i * kvec] / dplus[(size_t)i * kvec + v];
+                    xi = (i == be - 1) ? yi : yi - (e[i] / dplus[(size_t)i * kvec + v]) * xi;
+                    if (fabs(xi) > big) {
+                        for (int j = i + 1; j < be; ++j) x[(size_t)j * kvec] *= shrink;
+                        for (int j = bs; j < i; ++j) x[(size_t)j * kvec] *= shrink;
+                        xi *= shrink;
+                    }
+                    x[(size_t)i * kvec] = xi;
+                }
+                double mx = 0.0;
+                for (int i = bs; i < be; ++i) mx = fmax(mx, fabs(x[(size_t)i * kvec]));
+                const double sc = (mx > 0.0 && mx <= DBL_MAX) ? 1.0 / mx : 0.0;
+                for (int i = 0; i < n; ++i)
+                    zv[i] = (i >= bs && i < be) ? (T)(x[(size_t)i * kvec] * sc) : T(0);
             }
+            __syncthreads();
+            double nr = 0.0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) nr += (double)zv[i] * (double)zv[i];
+            nr = block_sum(nr, red);
+            const double inv = (nr > 0.0) ? 1.0 / sqrt(nr) : 0.0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) zv[i] = (T)((double)zv[i] * inv);
+            __syncthreads();
+            s = cluster_project(n, i0, v, z, ldz, red);
         }
-        double s = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)zv[i] * (double)zv[i];
-        s = block_sum(s, red);
         if (s < 1e-4) {
             if (threadIdx.x == 0) report_error(status, ELSI_ERR_NO_CONVERGENCE, v);
             return;
         }
-        double inv = 1.0 / sqrt(s);
+        const double inv = 1.0 / sqrt(s);
         for (int i = threadIdx.x; i < n; i += blockDim.x) zv[i] = (T)((double)zv[i] * inv);
         __syncthreads();
     }
@@ -334,7 +399,8 @@ cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int 
     twisted_kernel<T><<<ceil_div(kvec, 64), 64, 0, st>>>(n, d, e, kvec, w, bounds, blk, z, ldz, scratch,
                                                         scratch + (size_t)n * kvec, status);
     EGB_COUNT_LAUNCH();
-    cluster_orth_kernel<T><<<kvec, 256, 0, st>>>(n, kvec, w, bounds, 1e-5, z, ldz, status);
+    cluster_orth_kernel<T><<<kvec, 256, 0, st>>>(n, kvec, w, e, bounds, blk, 1e-5, scratch,
+                                                 scratch + (size_t)n * kvec, z, ldz, status);
     return cudaGetLastError();
 }
 
