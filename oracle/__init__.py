@@ -16,8 +16,13 @@ Each routine follows arXiv:1705.11191 (ELSI):
   back_substitute Eq. 9 (c = L^{-*} c~)
   occupation      sec. 4.4 (elsi_dm_real): bisection for mu, Eqs. 14-15, 17-18, and
                   the exact-charge correction
+  occupation_weighted
+                  sec. 4.4: one mu for several k-points / spin channels (the electron
+                  count summed over all of them, each problem with its weight)
   weighted_outer  Eq. 7 (density matrix) and its energy-weighted form W
   solve           the whole path
+  solve_batched   several independent problems (k-points / spin channels, sec. 2's
+                  SINGLE_PROC mode) with a shared or a per-problem chemical potential
 """
 from __future__ import annotations
 
@@ -72,6 +77,8 @@ def _load():
             lib.orc_solve.argtypes = [i, i, _dp, _dp, i, d, i, d, d, i,
                                       _dp, _dp, _dp, _dp, _dp, _dp, _dp]
             lib.orc_solve.restype = i
+            lib.orc_occupation_weighted.argtypes = [i, _dp, _dp, d, i, d, d, i, _dp, _dp]
+            lib.orc_occupation_weighted.restype = i
             lib.orc_num_threads.argtypes = []
             lib.orc_num_threads.restype = i
             _lib = lib
@@ -153,6 +160,24 @@ def occupation(eps, n_el: float, scheme: int = SCHEME_INTEGER, kt: float = 0.0,
     return f, mu.value
 
 
+def occupation_weighted(eps, wt, n_el: float, scheme: int = SCHEME_INTEGER, kt: float = 0.0,
+                        occ_accuracy: float = 1e-12, mu_max_steps: int = 200):
+    """One chemical potential over weighted entries (any order). Returns (f, mu)."""
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    wt = np.ascontiguousarray(wt, dtype=np.float64)
+    m = eps.shape[0]
+    if wt.shape != (m,):
+        raise ValueError("eps and wt differ in length")
+    f = np.zeros(m)
+    mu = ctypes.c_double(0.0)
+    rc = _load().orc_occupation_weighted(m, _ptr(eps), _ptr(wt), float(n_el), int(scheme),
+                                         float(kt), float(occ_accuracy), int(mu_max_steps),
+                                         _ptr(f), ctypes.byref(mu))
+    if rc:
+        raise OracleError("weighted occupation failed")
+    return f, mu.value
+
+
 def weighted_outer(c, w):
     """sum_l w_l c_l c_l^T over the columns of c."""
     c = _f64(c)
@@ -229,3 +254,52 @@ def solve_complex(h, s, n_state: int, n_el: float, *, unit_ovlp: bool = False,
         out["P"] = pe[:n, :n] + 1j * pe[n:, :n]
         out["W"] = we[:n, :n] + 1j * we[n:, :n]
     return out
+
+
+def solve_batched(problems, n_el, *, weights=None, shared_mu: bool = True,
+                  is_complex: bool = False, scheme: int = SCHEME_INTEGER, kt: float = 0.0,
+                  occ_accuracy: float = 1e-12, mu_max_steps: int = 200, want_pw: bool = True):
+    """Independent problems (h_i, s_i, n_state_i) solved one after another (sec. 2,
+    SINGLE_PROC: one process handles several k-points in turn), then occupied:
+      shared_mu: one mu with sum_i weights[i] sum_l f_il = n_el (a number);
+      otherwise: problem i on its own with n_el[i] electrons.
+    P_i = sum_l f_il c_il c_il^H and W_i = sum_l f_il eps_il c_il c_il^H (unweighted: the
+    total density of a k-point sum is sum_i weights[i] P_i). Returns a list of dicts
+    (eval, C, f, P, W, energy) and the chemical potential(s)."""
+    out = []
+    for (h, s, k) in problems:
+        if is_complex:
+            r = solve_complex(h, s, k, 2.0 * k, unit_ovlp=s is None, want_pw=False)
+        else:
+            r = solve(h, s, k, 2.0 * k, unit_ovlp=s is None, want_pw=False)
+        out.append(dict(eval=r["eval"], C=r["C"]))
+    if shared_mu:
+        wts = np.ones(len(problems)) if weights is None else np.asarray(weights, dtype=float)
+        eps = np.concatenate([o["eval"][:k] for o, (_, _, k) in zip(out, problems)])
+        wt = np.concatenate([np.full(k, wts[i]) for i, (_, _, k) in enumerate(problems)])
+        f, mu = occupation_weighted(eps, wt, float(n_el), scheme=scheme, kt=kt,
+                                    occ_accuracy=occ_accuracy, mu_max_steps=mu_max_steps)
+        off = 0
+        for o, (_, _, k) in zip(out, problems):
+            o["f"] = f[off:off + k]
+            off += k
+        mus = mu
+    else:
+        mus = []
+        for i, (o, (_, _, k)) in enumerate(zip(out, problems)):
+            f, mu = occupation(o["eval"][:k], float(n_el[i]), scheme=scheme, kt=kt,
+                               occ_accuracy=occ_accuracy, mu_max_steps=mu_max_steps)
+            o["f"] = f
+            mus.append(mu)
+    for o, (_, _, k) in zip(out, problems):
+        ev = o["eval"][:k]
+        o["energy"] = float(np.sum(o["f"] * ev))
+        if want_pw:
+            c = o["C"]
+            if is_complex:
+                o["P"] = (c * o["f"]) @ c.conj().T
+                o["W"] = (c * (o["f"] * ev)) @ c.conj().T
+            else:
+                o["P"] = weighted_outer(c, o["f"])
+                o["W"] = weighted_outer(c, o["f"] * ev)
+    return out, mus

@@ -314,6 +314,112 @@ int orc_occupation(int k, const double *eps, double n_el, int scheme, double kt,
 }
 
 /* ------------------------------------------------------------------------------------
+ * One chemical potential for several problems (k-points and spin channels). Sec. 4.4
+ * states that the electron count of the bisection is summed over k-points, spin
+ * channels and states. Entry j (of m, in any order) has eigenvalue eps[j] and weight
+ * wt[j] >= 0 (the weight of the problem it belongs to); the electron count is
+ * sum_j wt[j] f_j with f_j in [0, g].
+ *   Integer occupation: aufbau, levels in ascending order of eigenvalue; a level is the
+ *   set of entries with exactly equal eigenvalues, and the top level shares the
+ *   electrons left in proportion to the weights. mu = eigenvalue of the top level that
+ *   receives electrons (the lowest eigenvalue when n_el = 0).
+ *   Smeared occupation: bisection as in orc_occupation with the weighted count. When it
+ *   stalls, mu = hi and the surplus is removed from the levels in descending order, a
+ *   whole level at a time, the last one scaled by a common factor.
+ * Returns 0, or -1 for invalid arguments.
+ * ---------------------------------------------------------------------------------- */
+static const double *g_sort_key;
+static int cmp_by_key(const void *a, const void *b)
+{
+    int i = *(const int *)a, j = *(const int *)b;
+    if (g_sort_key[i] < g_sort_key[j]) return -1;
+    if (g_sort_key[i] > g_sort_key[j]) return 1;
+    return (i > j) - (i < j);
+}
+
+static double wocc_count(int m, const double *eps, const double *wt, int scheme, double kt,
+                         double mu, double g)
+{
+    double s = 0.0;
+    for (int j = 0; j < m; ++j) s += wt[j] * g * occ_phi(scheme, (eps[j] - mu) / kt);
+    return s;
+}
+
+int orc_occupation_weighted(int m, const double *eps, const double *wt, double n_el,
+                            int scheme, double kt, double occ_accuracy, int mu_max_steps,
+                            double *f, double *mu_out)
+{
+    const double g = 2.0;
+    if (m <= 0 || n_el < 0.0) return -1;
+    double wsum = 0.0;
+    for (int j = 0; j < m; ++j) {
+        if (!(wt[j] >= 0.0)) return -1;
+        wsum += wt[j];
+    }
+    if (n_el > g * wsum * (1.0 + 1e-14)) return -1;
+    int *ord = (int *)malloc(sizeof(int) * (size_t)m);
+    for (int j = 0; j < m; ++j) ord[j] = j;
+    g_sort_key = eps;
+    qsort(ord, (size_t)m, sizeof(int), cmp_by_key); /* ascending eigenvalue */
+    if (scheme == 0) {
+        double left = n_el;
+        double mu = eps[ord[0]];
+        for (int a = 0; a < m;) {
+            int b = a;
+            double wl = 0.0;
+            while (b < m && eps[ord[b]] == eps[ord[a]]) wl += wt[ord[b++]];
+            double fl;
+            if (left <= 0.0) fl = 0.0;
+            else if (left >= g * wl) fl = g;
+            else fl = left / wl;
+            if (left > 0.0) mu = eps[ord[a]];
+            for (int c = a; c < b; ++c) f[ord[c]] = fl;
+            left -= fl * wl;
+            a = b;
+        }
+        *mu_out = mu;
+        free(ord);
+        return 0;
+    }
+    if (!(kt > 0.0) || (scheme != 1 && scheme != 2)) { free(ord); return -1; }
+    double lo = eps[ord[0]], hi = eps[ord[m - 1]];
+    for (int it = 0; it < 1000 && wocc_count(m, eps, wt, scheme, kt, lo, g) > n_el; ++it) lo -= 1.0;
+    for (int it = 0; it < 1000 && wocc_count(m, eps, wt, scheme, kt, hi, g) < n_el; ++it) hi += 1.0;
+    double mu = hi;
+    int converged = 0;
+    for (int step = 0; step < mu_max_steps; ++step) {
+        double mid = 0.5 * (lo + hi);
+        double nm = wocc_count(m, eps, wt, scheme, kt, mid, g);
+        if (fabs(nm - n_el) <= occ_accuracy) { mu = mid; converged = 1; break; }
+        if (nm < n_el) lo = mid; else hi = mid;
+    }
+    if (!converged) mu = hi;
+    for (int j = 0; j < m; ++j) f[j] = g * occ_phi(scheme, (eps[j] - mu) / kt);
+    if (!converged) {
+        double surplus = -n_el;
+        for (int j = 0; j < m; ++j) surplus += wt[j] * f[j];
+        double removed = 0.0;
+        for (int b = m; b > 0 && surplus > 0.0;) {
+            int a = b - 1;
+            while (a > 0 && eps[ord[a - 1]] == eps[ord[b - 1]]) --a;
+            double gl = 0.0;
+            for (int c = a; c < b; ++c) gl += wt[ord[c]] * f[ord[c]];
+            if (removed + gl >= surplus) {
+                double keep = (gl > 0.0) ? 1.0 - (surplus - removed) / gl : 0.0;
+                for (int c = a; c < b; ++c) f[ord[c]] *= keep;
+                break;
+            }
+            for (int c = a; c < b; ++c) f[ord[c]] = 0.0;
+            removed += gl;
+            b = a;
+        }
+    }
+    *mu_out = mu;
+    free(ord);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
  * Weighted outer-product sum D = sum_l w_l c_l c_l^T over the first k columns of c.
  * With w = f this is the density matrix (Eq. 7, "eq:density_matrix", sec. 2);
  * with w = f*eps it is the energy-weighted density matrix W.
