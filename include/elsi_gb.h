@@ -157,6 +157,66 @@ int elsi_get_refine_info(elsi_handle h, int *iters, double *orth_err);
 int elsi_density_noalloc(int n_basis, int n_state, const double *evec, const double *occ,
                          const double *eval, double *den_mat, double *edm, void *stream);
 
+/* ---- Several problems: k-points and spin channels ----------------------------------
+ * Sec. 2 (SINGLE_PROC mode): one process solves a group of k-points one after another;
+ * sec. 4.4: the chemical potential's electron count is summed over k-points, spin
+ * channels and states. Problem i has n_basis[i] basis functions and n_state[i] states
+ * (host int arrays); ham[i] and ovlp[i] are DEVICE pointers to its n_basis[i]^2 matrices
+ * (column-major; interleaved complex for the _complex calls), passed in HOST arrays of
+ * nprob pointers. ovlp (or any ovlp[i]) may be NULL only with overlap_is_unit set.
+ * The handle's settings (broadening, width, accuracy, precision, band width, stream)
+ * apply to every problem; its own n_basis, n_state, n_electron are not used. The
+ * eigenpairs stay in the handle until the next batched call or elsi_finalize.
+ *
+ * elsi_dm_batched_real / _complex: all three phases below in one call.
+ *   shared_mu = 1: one chemical potential with
+ *       sum_i weight[i] sum_l f_il = n_electron[0]      (weight: host, nprob values >= 0,
+ *       e.g. k-point weights; f_il in [0, 2] is the occupation of state l of problem i);
+ *     integer occupation then fills the levels of all problems in ascending order, a
+ *     level (entries with exactly equal eigenvalues) sharing the remaining electrons in
+ *     proportion to the weights; smeared occupation bisects on the weighted count.
+ *   shared_mu = 0: problem i is occupied on its own with n_electron[i] electrons
+ *     (<= 2 n_state[i]) and its own chemical potential; weight may be NULL.
+ *   Outputs: den_mat[i] (device, n_basis[i]^2) = P_i = sum_l f_il c_il c_il^H, edm[i]
+ *   (device, may be NULL or the array NULL) = W_i = sum_l f_il eps_il c_il c_il^H, both
+ *   unweighted (the k-summed density is sum_i weight[i] P_i); energy (host, nprob, may
+ *   be NULL) = sum_l f_il eps_il per problem; mu (host, may be NULL): 1 value when
+ *   shared_mu, else nprob.
+ *   Errors: ELSI_ERR_ARG (sizes, null pointers, negative weight, electron count outside
+ *   [0, 2 sum of weights x states]), the single-problem codes of any problem (message
+ *   names the problem), ELSI_ERR_NOMEM, ELSI_ERR_CUDA. */
+int elsi_dm_batched_real(elsi_handle h, int nprob, const int *n_basis, const int *n_state,
+                         const double *const *ham, const double *const *ovlp,
+                         const double *weight, const double *n_electron, int shared_mu,
+                         double *const *den_mat, double *const *edm, double *energy, double *mu);
+int elsi_dm_batched_complex(elsi_handle h, int nprob, const int *n_basis, const int *n_state,
+                            const double *const *ham, const double *const *ovlp,
+                            const double *weight, const double *n_electron, int shared_mu,
+                            double *const *den_mat, double *const *edm, double *energy,
+                            double *mu);
+
+/* Phase 1: eigenpairs of every problem, kept in the handle. eval (device, may be NULL)
+ * receives the n_state[i] lowest eigenvalues of each problem, concatenated in problem
+ * order (sum_i n_state[i] doubles). */
+int elsi_batch_ev_real(elsi_handle h, int nprob, const int *n_basis, const int *n_state,
+                       const double *const *ham, const double *const *ovlp, double *eval);
+int elsi_batch_ev_complex(elsi_handle h, int nprob, const int *n_basis, const int *n_state,
+                          const double *const *ham, const double *const *ovlp, double *eval);
+
+/* Phase 2: occupations with one chemical potential over m weighted entries (device
+ * arrays eps, weight, occ of length m, any order; the eigenvalues of several problems,
+ * possibly gathered from several processes). sum_j weight[j] occ[j] = n_electron with
+ * occ[j] in [0, 2]; rules as for shared_mu above. mu: host, may be NULL. */
+int elsi_occupation_weighted(elsi_handle h, int m, const double *eps, const double *weight,
+                             double n_electron, double *occ, double *mu);
+
+/* Phase 3: P_i and W_i of the problems of the last elsi_batch_ev_* call from the
+ * occupations occ (device, laid out like that call's eval). Outputs as for
+ * elsi_dm_batched_*: real matrices after _real, interleaved complex after _complex.
+ * ELSI_ERR_STATE without a preceding batched eigensolve. */
+int elsi_batch_dm(elsi_handle h, const double *occ, double *const *den_mat,
+                  double *const *edm, double *energy);
+
 /* Message describing the last error on this handle ("" if none). */
 const char *elsi_get_last_error(elsi_handle h);
 

@@ -33,6 +33,7 @@ ERR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_UNSUPPORTED", 3: "ERR_NOT_PD",
 _lib = None
 _lock = threading.Lock()
 _vp, _dp, _ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+_pp = ctypes.POINTER(ctypes.c_void_p)
 
 
 class ElsiError(RuntimeError):
@@ -73,6 +74,12 @@ def _declare(lib):
         "elsi_gb_version": ([], ctypes.c_char_p),
         "elsi_gb_launch_count": ([], ctypes.c_longlong),
         "elsi_density_noalloc": ([i, i, _vp, _vp, _vp, _vp, _vp, _vp], i),
+        "elsi_dm_batched_real": ([H, i, _ip, _ip, _pp, _pp, _dp, _dp, i, _pp, _pp, _dp, _dp], i),
+        "elsi_dm_batched_complex": ([H, i, _ip, _ip, _pp, _pp, _dp, _dp, i, _pp, _pp, _dp, _dp], i),
+        "elsi_batch_ev_real": ([H, i, _ip, _ip, _pp, _pp, _vp], i),
+        "elsi_batch_ev_complex": ([H, i, _ip, _ip, _pp, _pp, _vp], i),
+        "elsi_occupation_weighted": ([H, i, _vp, _vp, d, _vp, _dp], i),
+        "elsi_batch_dm": ([H, _vp, _pp, _pp, _dp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -291,6 +298,86 @@ class Handle:
                                          _vp(hp(edm)), ctypes.byref(e))
         self._check(rc, "elsi_dm_real_host")
         return e.value
+
+    # ---- several problems (k-points / spin channels) ----
+    def _batch_inputs(self, hams, ovlps, n_states):
+        import torch
+        cplx = hams[0].is_complex()
+        dt = torch.complex128 if cplx else torch.float64
+        prep = (lambda t: _colmajor(t)) if cplx else (lambda t: t)
+        hs = [prep(t) for t in hams]
+        ss = None if ovlps is None else [prep(t) for t in ovlps]
+        nprob = len(hs)
+        nb = (ctypes.c_int * nprob)(*[int(t.shape[0]) for t in hs])
+        ks = (ctypes.c_int * nprob)(*[int(k) for k in n_states])
+        hp = (_vp * nprob)(*[_ptr(t, dt) for t in hs])
+        sp = None if ss is None else (_vp * nprob)(*[_ptr(t, dt) for t in ss])
+        self._batch = dict(n=[int(t.shape[0]) for t in hs], k=[int(k) for k in n_states],
+                           cplx=cplx, device=hs[0].device)
+        return cplx, dt, hs, ss, nb, ks, hp, sp
+
+    def _batch_outputs(self, want_edm):
+        import torch
+        b = getattr(self, "_batch", None)
+        if b is None:  # no batched eigensolve yet: the library reports ELSI_ERR_STATE
+            b = dict(n=[], k=[], cplx=False, device="cuda")
+        dt = torch.complex128 if b["cplx"] else torch.float64
+        ps = [torch.empty((n, n), dtype=dt, device=b["device"]) for n in b["n"]]
+        ws = [torch.empty((n, n), dtype=dt, device=b["device"]) for n in b["n"]] if want_edm else None
+        nprob = len(ps)
+        pp = (_vp * max(nprob, 1))(*[_ptr(t, dt) for t in ps])
+        wp = (_vp * max(nprob, 1))(*[_ptr(t, dt) for t in ws]) if want_edm else None
+        fix = (lambda t: t.t()) if b["cplx"] else (lambda t: t)
+        return ps, ws, pp, wp, fix
+
+    def dm_batched(self, hams, ovlps, n_states, n_electron, *, weights=None,
+                   shared_mu: bool = True, want_edm: bool = True):
+        """Density matrices of several problems (real float64 or complex128 CUDA tensors).
+        shared_mu: one chemical potential, sum_i weights[i] sum_l f_il = n_electron;
+        else n_electron is a list, one per problem. Returns (P list, W list or None,
+        band energies, mu (float, or list))."""
+        cplx, dt, hs, ss, nb, ks, hp, sp = self._batch_inputs(hams, ovlps, n_states)
+        nprob = len(hs)
+        ps, ws, pp, wp, fix = self._batch_outputs(want_edm)
+        wts = None if weights is None else (ctypes.c_double * nprob)(*[float(w) for w in weights])
+        nel = [float(n_electron)] if shared_mu else [float(x) for x in n_electron]
+        nel_a = (ctypes.c_double * len(nel))(*nel)
+        en = (ctypes.c_double * nprob)()
+        mu = (ctypes.c_double * nprob)()
+        fn = self._lib.elsi_dm_batched_complex if cplx else self._lib.elsi_dm_batched_real
+        rc = fn(self._h, nprob, nb, ks, hp, sp, wts, nel_a, int(bool(shared_mu)), pp, wp, en, mu)
+        self._check(rc, fn.__name__)
+        mus = mu[0] if shared_mu else list(mu)
+        return ([fix(p) for p in ps], [fix(w) for w in ws] if want_edm else None, list(en), mus)
+
+    def batch_ev(self, hams, ovlps, n_states):
+        """Phase 1: eigenpairs of every problem, kept in the handle. Returns the
+        n_states[i] lowest eigenvalues of each problem, concatenated (CUDA tensor)."""
+        import torch
+        cplx, dt, hs, ss, nb, ks, hp, sp = self._batch_inputs(hams, ovlps, n_states)
+        ev = torch.empty(sum(self._batch["k"]), dtype=torch.float64, device=hs[0].device)
+        fn = self._lib.elsi_batch_ev_complex if cplx else self._lib.elsi_batch_ev_real
+        self._check(fn(self._h, len(hs), nb, ks, hp, sp, _vp(_ptr(ev))), fn.__name__)
+        return ev
+
+    def occupation_weighted(self, eps, wts, n_electron: float):
+        """Phase 2: occupations (CUDA tensor) and one chemical potential over weighted
+        eigenvalues (CUDA float64 tensors of equal length)."""
+        import torch
+        f = torch.empty_like(eps)
+        mu = ctypes.c_double(0.0)
+        rc = self._lib.elsi_occupation_weighted(self._h, int(eps.numel()), _vp(_ptr(eps)),
+                                                _vp(_ptr(wts)), float(n_electron), _vp(_ptr(f)),
+                                                ctypes.byref(mu))
+        self._check(rc, "elsi_occupation_weighted")
+        return f, mu.value
+
+    def batch_dm(self, occ, want_edm: bool = True):
+        """Phase 3: (P list, W list or None, band energies) of the last batch_ev."""
+        ps, ws, pp, wp, fix = self._batch_outputs(want_edm)
+        en = (ctypes.c_double * len(ps))()
+        self._check(self._lib.elsi_batch_dm(self._h, _vp(_ptr(occ)), pp, wp, en), "elsi_batch_dm")
+        return [fix(p) for p in ps], [fix(w) for w in ws] if want_edm else None, list(en)
 
     def stage_times(self) -> dict:
         buf = (ctypes.c_float * 32)()

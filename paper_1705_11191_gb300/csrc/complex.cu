@@ -75,6 +75,40 @@ static int grid_of(size_t total)
     return (int)(g ? g : 1);
 }
 
+__global__ void dup_pairs_kernel(int n, const double *__restrict__ f, double *__restrict__ f2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        f2[2 * i] = f2[2 * i + 1] = f[i];
+}
+
+cudaError_t embed_hermitian(cudaStream_t st, int n, const double *src, double *dst)
+{
+    EGB_COUNT_LAUNCH();
+    embed_hermitian_kernel<<<grid_of(4 * (size_t)n * n), 256, 0, st>>>(n, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t fold_hermitian(cudaStream_t st, int n, const double *emb, double *dst)
+{
+    EGB_COUNT_LAUNCH();
+    fold_hermitian_kernel<<<grid_of((size_t)n * n), 256, 0, st>>>(n, emb, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t pair_evals(cudaStream_t st, int n, const double *w2, double *w)
+{
+    EGB_COUNT_LAUNCH();
+    pair_eval_kernel<<<grid_of(n), 256, 0, st>>>(n, w2, w);
+    return cudaGetLastError();
+}
+
+cudaError_t dup_pairs(cudaStream_t st, int n, const double *f, double *f2)
+{
+    EGB_COUNT_LAUNCH();
+    dup_pairs_kernel<<<grid_of(n), 256, 0, st>>>(n, f, f2);
+    return cudaGetLastError();
+}
+
 // Internal handle of size 2n with the parent's settings.
 elsi_gb_handle_s *complex_handle(elsi_gb_handle_s *h)
 {
@@ -82,12 +116,13 @@ elsi_gb_handle_s *complex_handle(elsi_gb_handle_s *h)
         h->cplx = new (std::nothrow) elsi_gb_handle_s();
         if (!h->cplx) return nullptr;
         h->cplx->magic = kHandleMagic;
-        h->cplx->n = 2 * h->n;
-        h->cplx->n_state = 2 * h->n_state;
-        h->cplx->n_electron = 2.0 * h->n_electron;
         h->cplx->occ_stride = 2;
     }
     elsi_gb_handle_s *c = h->cplx;
+    if (c->n != 2 * h->n) c->have_l = false;
+    c->n = 2 * h->n;
+    c->n_state = 2 * h->n_state;
+    c->n_electron = 2.0 * h->n_electron;
     c->overlap_is_unit = h->overlap_is_unit;
     c->scheme = h->scheme;
     c->kt = h->kt;

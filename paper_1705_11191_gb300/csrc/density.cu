@@ -1,6 +1,8 @@
 // Occupation numbers, chemical potential, band energy (arXiv:1705.11191 sec. 4.4,
 // elsi_dm_real; Eqs. 14-15 and 17-18) and the density matrices P = C diag(f) C^T
 // (Eq. 7) and W = C diag(f eps) C^T.
+#include <cfloat>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -93,6 +95,191 @@ cudaError_t occupation(cudaStream_t st, int k, const double *eps, double n_el, i
     EGB_COUNT_LAUNCH();
     occupation_kernel<<<1, 1024, 0, st>>>(k, eps, n_el, scheme, kt, occ_accuracy, mu_max_steps, f,
                                           out, status, stride);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ double block_max(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    double s = (lane < nw) ? red[lane] : -DBL_MAX;
+    if (warp == 0) {
+        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        if (lane == 0) red[0] = s;
+    }
+    __syncthreads();
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// One chemical potential for m weighted entries of several problems (k-points, spin
+// channels; sec. 4.4 sums the electron count of the bisection over them). Entry j has
+// eigenvalue eps[j] and weight wt[j]; the count is sum_j wt[j] f_j, f_j in [0, 2]. The
+// entries need not be sorted: where an order is needed (aufbau filling, surplus
+// removal) the level that the rule stops at is isolated by bisection on the eigenvalue
+// axis until the interval holds a single distinct eigenvalue. Entries with exactly equal
+// eigenvalues form one level and are treated alike. One CTA.
+// out[0] = mu, out[1] = sum_j wt[j] f_j eps[j].
+__global__ void occupation_weighted_kernel(int m, const double *eps, const double *wt, double n_el,
+                                           int scheme, double kt, double occ_accuracy,
+                                           int mu_max_steps, double *f, double *out, int *status)
+{
+    __shared__ double red[32];
+    const double g = 2.0;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double mn = DBL_MAX, mx = -DBL_MAX, ws = 0.0;
+    for (int j = tid; j < m; j += nt) {
+        mn = fmin(mn, eps[j]);
+        mx = fmax(mx, eps[j]);
+        ws += wt[j];
+    }
+    mn = -block_max(-mn, red);
+    mx = block_max(mx, red);
+    ws = block_sum(ws, red);
+    if (!(n_el >= 0.0) || n_el > g * ws * (1.0 + 1e-14)) {
+        if (tid == 0) report_error(status, ELSI_ERR_ARG, 0);
+        return;
+    }
+    // distinct eigenvalues in (lo, hi] (lower_open) or [lo, hi): min and max of them
+    auto range_in = [&](double lo, double hi, bool lower_open, double &a, double &b) {
+        double x = DBL_MAX, y = -DBL_MAX;
+        for (int j = tid; j < m; j += nt) {
+            const double v = eps[j];
+            const bool in = lower_open ? (v > lo && v <= hi) : (v >= lo && v < hi);
+            if (in) { x = fmin(x, v); y = fmax(y, v); }
+        }
+        a = -block_max(-x, red);
+        b = block_max(y, red);
+    };
+    double mu;
+    if (scheme == ELSI_OCC_INTEGER) {
+        if (n_el <= 0.0) {
+            for (int j = tid; j < m; j += nt) f[j] = 0.0;
+            mu = mn;
+        } else {
+            // smallest level e* with N(<= e*) >= n_el; invariant N(<= lo) < n_el <= N(<= hi)
+            auto n_le = [&](double x) {
+                double s = 0.0;
+                for (int j = tid; j < m; j += nt) s += (eps[j] <= x) ? g * wt[j] : 0.0;
+                return block_sum(s, red);
+            };
+            double lo = mn - 1.0, hi = mx, estar = mx;
+            bool found = false;
+            for (int it = 0; it < 4096; ++it) {
+                double a, b;
+                range_in(lo, hi, true, a, b);
+                if (a == b) { estar = a; found = true; break; }
+                const double mid = 0.5 * (lo + hi);
+                if (n_le(mid) >= n_el) hi = mid; else lo = mid;
+            }
+            if (!found && tid == 0) report_error(status, ELSI_ERR_NO_CONVERGENCE, 0);
+            double below = 0.0, wl = 0.0;
+            for (int j = tid; j < m; j += nt) {
+                if (eps[j] < estar) below += g * wt[j];
+                else if (eps[j] == estar) wl += wt[j];
+            }
+            below = block_sum(below, red);
+            wl = block_sum(wl, red);
+            const double fl = (wl > 0.0) ? fmin(g, fmax(0.0, (n_el - below) / wl)) : 0.0;
+            for (int j = tid; j < m; j += nt)
+                f[j] = (eps[j] < estar) ? g : ((eps[j] == estar) ? fl : 0.0);
+            mu = estar;
+        }
+    } else {
+        auto count = [&](double x) {
+            double s = 0.0;
+            for (int j = tid; j < m; j += nt) s += wt[j] * g * occ_phi(scheme, (eps[j] - x) / kt);
+            return block_sum(s, red);
+        };
+        double lo = mn, hi = mx;
+        for (int it = 0; it < 1000 && count(lo) > n_el; ++it) lo -= 1.0;
+        for (int it = 0; it < 1000 && count(hi) < n_el; ++it) hi += 1.0;
+        mu = hi;
+        bool converged = false;
+        for (int step = 0; step < mu_max_steps; ++step) {
+            const double mid = 0.5 * (lo + hi);
+            const double nm = count(mid);
+            if (fabs(nm - n_el) <= occ_accuracy) { mu = mid; converged = true; break; }
+            if (nm < n_el) lo = mid; else hi = mid;
+        }
+        if (!converged) mu = hi;
+        for (int j = tid; j < m; j += nt) f[j] = g * occ_phi(scheme, (eps[j] - mu) / kt);
+        __syncthreads();
+        if (!converged) {
+            double sur = 0.0;
+            for (int j = tid; j < m; j += nt) sur += wt[j] * f[j];
+            const double surplus = block_sum(sur, red) - n_el;
+            if (surplus > 0.0) {
+                // highest level x* with S(>= x*) >= surplus, S(>= x) = sum_{eps >= x} wt f
+                auto s_ge = [&](double x) {
+                    double s = 0.0;
+                    for (int j = tid; j < m; j += nt) s += (eps[j] >= x) ? wt[j] * f[j] : 0.0;
+                    return block_sum(s, red);
+                };
+                double lo2 = mn, hi2 = fmax(mx + 1.0, mx * (1.0 + 1e-15) + 1.0), xs = mn;
+                bool found = false;
+                for (int it = 0; it < 4096; ++it) {
+                    double a, b;
+                    range_in(lo2, hi2, false, a, b);
+                    if (a == b) { xs = a; found = true; break; }
+                    const double mid = 0.5 * (lo2 + hi2);
+                    if (s_ge(mid) >= surplus) lo2 = mid; else hi2 = mid;
+                }
+                if (!found && tid == 0) report_error(status, ELSI_ERR_NO_CONVERGENCE, 1);
+                double gt = 0.0, gl = 0.0;
+                for (int j = tid; j < m; j += nt) {
+                    if (eps[j] > xs) gt += wt[j] * f[j];
+                    else if (eps[j] == xs) gl += wt[j] * f[j];
+                }
+                gt = block_sum(gt, red);
+                gl = block_sum(gl, red);
+                const double keep = (gl > 0.0) ? 1.0 - (surplus - gt) / gl : 0.0;
+                for (int j = tid; j < m; j += nt) {
+                    if (eps[j] > xs) f[j] = 0.0;
+                    else if (eps[j] == xs) f[j] *= keep;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    double es = 0.0;
+    for (int j = tid; j < m; j += nt) es += wt[j] * f[j] * eps[j];
+    es = block_sum(es, red);
+    if (tid == 0) { out[0] = mu; out[1] = es; }
+}
+
+cudaError_t occupation_weighted(cudaStream_t st, int m, const double *eps, const double *wt,
+                                double n_el, int scheme, double kt, double occ_accuracy,
+                                int mu_max_steps, double *f, double *out, int *status)
+{
+    EGB_COUNT_LAUNCH();
+    occupation_weighted_kernel<<<1, 1024, 0, st>>>(m, eps, wt, n_el, scheme, kt, occ_accuracy,
+                                                   mu_max_steps, f, out, status);
+    return cudaGetLastError();
+}
+
+// Band energy of each problem of a batch: out[i] = sum over its entries of f * eps
+// (entries off[i] .. off[i+1]-1). One CTA per problem.
+__global__ void segment_energy_kernel(const int *off, const double *f, const double *eps, double *out)
+{
+    __shared__ double red[32];
+    const int i = blockIdx.x;
+    double s = 0.0;
+    for (int j = off[i] + threadIdx.x; j < off[i + 1]; j += blockDim.x) s += f[j] * eps[j];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[i] = s;
+}
+
+cudaError_t segment_energy(cudaStream_t st, int nseg, const int *off, const double *f,
+                           const double *eps, double *out)
+{
+    EGB_COUNT_LAUNCH();
+    segment_energy_kernel<<<nseg, 256, 0, st>>>(off, f, eps, out);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,7 @@ int elsi_finalize(elsi_handle *hp)
     if (!hp || check_handle(*hp)) return ELSI_ERR_STATE;
     elsi_gb_handle_s *h = *hp;
     free_complex(h);
+    free_batch(h);
     free_workspace(h);
     h->magic = 0;
     delete h;
@@ -218,6 +219,57 @@ int elsi_get_edm_complex(elsi_handle h, double *edm)
     if (check_handle(h)) return ELSI_ERR_STATE;
     if (!edm) return set_error(h, ELSI_ERR_ARG, "null pointer argument");
     return get_edm_complex(h, edm);
+}
+
+int elsi_dm_batched_real(elsi_handle h, int nprob, const int *n_basis, const int *n_state,
+                         const double *const *ham, const double *const *ovlp,
+                         const double *weight, const double *n_electron, int shared_mu,
+                         double *const *den_mat, double *const *edm, double *energy, double *mu)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    return dm_batched(h, nprob, n_basis, n_state, ham, ovlp, weight, n_electron, shared_mu,
+                      den_mat, edm, energy, mu, false);
+}
+
+int elsi_dm_batched_complex(elsi_handle h, int nprob, const int *n_basis, const int *n_state,
+                            const double *const *ham, const double *const *ovlp,
+                            const double *weight, const double *n_electron, int shared_mu,
+                            double *const *den_mat, double *const *edm, double *energy,
+                            double *mu)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    return dm_batched(h, nprob, n_basis, n_state, ham, ovlp, weight, n_electron, shared_mu,
+                      den_mat, edm, energy, mu, true);
+}
+
+int elsi_batch_ev_real(elsi_handle h, int nprob, const int *n_basis, const int *n_state,
+                       const double *const *ham, const double *const *ovlp, double *eval)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    return batch_ev(h, nprob, n_basis, n_state, ham, ovlp, false, eval);
+}
+
+int elsi_batch_ev_complex(elsi_handle h, int nprob, const int *n_basis, const int *n_state,
+                          const double *const *ham, const double *const *ovlp, double *eval)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    return batch_ev(h, nprob, n_basis, n_state, ham, ovlp, true, eval);
+}
+
+int elsi_occupation_weighted(elsi_handle h, int m, const double *eps, const double *weight,
+                             double n_electron, double *occ, double *mu)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (m < 1 || !eps || !weight || !occ) return set_error(h, ELSI_ERR_ARG, "null pointer or m < 1");
+    return batch_occupation(h, m, eps, weight, n_electron, occ, mu);
+}
+
+int elsi_batch_dm(elsi_handle h, const double *occ, double *const *den_mat, double *const *edm,
+                  double *energy)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!occ) return set_error(h, ELSI_ERR_ARG, "null occupation array");
+    return batch_dm(h, occ, den_mat, edm, energy);
 }
 
 int elsi_get_edm_real(elsi_handle h, double *edm)

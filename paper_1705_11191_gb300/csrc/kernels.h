@@ -105,10 +105,28 @@ cudaError_t apply_q1(cudaStream_t st, int n, int b, int k, const T *v1, const T 
 cudaError_t occupation(cudaStream_t st, int k, const double *eps, double n_el, int scheme,
                        double kt, double occ_accuracy, int mu_max_steps, double *f,
                        double *out /* [0]=mu [1]=energy */, int *status, int stride = 1);
+// One chemical potential over m weighted entries of several problems (see density.cu).
+cudaError_t occupation_weighted(cudaStream_t st, int m, const double *eps, const double *wt,
+                                double n_el, int scheme, double kt, double occ_accuracy,
+                                int mu_max_steps, double *f, double *out /* [0]=mu [1]=energy */,
+                                int *status);
+// out[i] = sum_{off[i] <= j < off[i+1]} f[j] eps[j] (off: device, nseg + 1 ints).
+cudaError_t segment_energy(cudaStream_t st, int nseg, const int *off, const double *f,
+                           const double *eps, double *out);
 // P = C diag(f) C^T and W = C diag(f eps) C^T (lower + mirror); cw: n x k scratch.
 template <typename T>
 cudaError_t density_pw(cudaStream_t st, int n, int k, const T *c, int ldc, const double *f,
                        const double *eps, T *p, T *w, T *cw);
+
+// ---- complex Hermitian problems through the real form (complex.cu) ----
+// dst (2n x 2n) = [[Re A, -Im A], [Im A, Re A]] of A (n x n, interleaved complex).
+cudaError_t embed_hermitian(cudaStream_t st, int n, const double *src, double *dst);
+// dst (n x n complex) = emb[0:n, 0:n] + i emb[n:2n, 0:n].
+cudaError_t fold_hermitian(cudaStream_t st, int n, const double *emb, double *dst);
+// w[i] = (w2[2i] + w2[2i+1]) / 2: one eigenvalue per pair of the real form.
+cudaError_t pair_evals(cudaStream_t st, int n, const double *w2, double *w);
+// f2[2i] = f2[2i+1] = f[i].
+cudaError_t dup_pairs(cudaStream_t st, int n, const double *f, double *f2);
 
 // ---- binary64-accurate products on the bf16 tensor cores (ozaki.cu) ----
 // Splits V vectors of length K (element (v, q) at src[v * sv + q * sq], optionally times

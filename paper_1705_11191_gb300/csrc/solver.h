@@ -56,6 +56,8 @@ struct Workspace {
     bool events_ready = false;
 };
 
+struct BatchState;
+
 }  // namespace egb
 
 struct elsi_gb_handle_s {
@@ -87,6 +89,8 @@ struct elsi_gb_handle_s {
     // complex Hermitian problems are solved as real ones of size 2n in this sub-handle
     elsi_gb_handle_s *cplx = nullptr;
     bool have_cedm = false;
+    // several independent problems (k-points / spin channels): batch.cu
+    egb::BatchState *batch = nullptr;
 };
 
 namespace egb {
@@ -108,5 +112,16 @@ int solve_complex(elsi_gb_handle_s *h, const double *ham, const double *ovlp, do
                   double *evec, double *den_mat, double *energy);
 int get_edm_complex(elsi_gb_handle_s *h, double *edm);
 void free_complex(elsi_gb_handle_s *h);
+void free_batch(elsi_gb_handle_s *h);
+int batch_ev(elsi_gb_handle_s *h, int nprob, const int *n_basis, const int *n_state,
+             const double *const *ham, const double *const *ovlp, bool cplx, double *eval);
+int batch_occupation(elsi_gb_handle_s *h, int m, const double *eps, const double *wt, double n_el,
+                     double *occ, double *mu);
+int batch_dm(elsi_gb_handle_s *h, const double *occ, double *const *dm, double *const *edm,
+             double *energy);
+int dm_batched(elsi_gb_handle_s *h, int nprob, const int *n_basis, const int *n_state,
+               const double *const *ham, const double *const *ovlp, const double *weight,
+               const double *n_electron, int shared_mu, double *const *dm, double *const *edm,
+               double *energy, double *mu, bool cplx);
 
 }  // namespace egb
