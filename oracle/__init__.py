@@ -303,3 +303,74 @@ def solve_batched(problems, n_el, *, weights=None, shared_mu: bool = True,
                 o["P"] = weighted_outer(c, o["f"])
                 o["W"] = weighted_outer(c, o["f"] * ev)
     return out, mus
+
+
+def entropy_term(eps, f, mu: float, scheme: int, kt: float) -> float:
+    """-kT S_ent, the entropy contribution to the Mermin free energy F = E_band - kT S_ent
+    (the paper names the broadening schemes, sec. 4.4, but gives no entropy; this is the
+    term for which dF/deps_l = f_l at fixed electron count, so that dF/dH = P):
+      Fermi-Dirac: S_ent = -g sum_l [phi ln phi + (1 - phi) ln(1 - phi)], phi = f_l / g;
+      Gaussian:    S_ent = g sum_l exp(-x_l^2) / (2 sqrt(pi)), x_l = (eps_l - mu) / kT;
+      integer:     0."""
+    g = 2.0
+    eps = np.asarray(eps, dtype=float)
+    f = np.asarray(f, dtype=float)
+    if scheme == SCHEME_INTEGER:
+        return 0.0
+    if scheme == SCHEME_FERMI:
+        phi = f / g
+        s = 0.0
+        for p in phi:
+            if 0.0 < p < 1.0:
+                s += p * np.log(p) + (1.0 - p) * np.log1p(-p)
+        return float(kt * g * s)
+    x = (eps - mu) / kt
+    return float(-kt * g * np.sum(np.exp(-x * x)) / (2.0 * np.sqrt(np.pi)))
+
+
+def free_energy(h, s, n_state: int, n_el: float, *, scheme: int = SCHEME_FERMI,
+                kt: float = 0.01, want_pw: bool = True, **kw):
+    """F = E_band - kT S_ent and the solve it comes from (dict of solve plus 'F')."""
+    r = solve(h, s, n_state, n_el, scheme=scheme, kt=kt, want_pw=want_pw, **kw)
+    r["F"] = r["energy"] + entropy_term(r["eval"][:n_state], r["f"], r["mu"], scheme, kt)
+    return r
+
+
+def ev_adjoint(ev, c, ev_bar=None, c_bar=None, guard: float = 1e-10):
+    """Reverse-mode derivative of the generalized symmetric eigenproblem H C = S C diag(ev),
+    C^T S C = I (all n eigenpairs in c), for a loss with dL/d ev = ev_bar (length n) and
+    dL/d C[:, :k] = c_bar (n x k). Perturbation theory (first order) gives, with
+    M = C^T dH C and N = C^T dS C,
+      d ev_j = M_jj - ev_j N_jj,
+      dC = C Omega,  Omega_ij = (M_ij - ev_j N_ij) / (ev_j - ev_i) (i != j),
+                     Omega_jj = -N_jj / 2,
+    so that dL = <X_H, M> + <X_S, N> with A = C^T c_bar (n x k), F_ij = 1/(ev_j - ev_i)
+    (0 for i = j or |ev_i - ev_j| < guard: the degeneracy guard),
+      X_H = diag(ev_bar) + [F o A | 0],
+      X_S = -diag(ev_bar ev) - [(F o A) diag(ev_k) | 0] - diag(A_jj / 2, j < k),
+    and dL/dH = C sym(X_H) C^T, dL/dS = C sym(X_S) C^T (sym(X) = (X + X^T)/2: the
+    gradient with respect to a symmetric matrix)."""
+    ev = np.asarray(ev, dtype=float)
+    c = np.asarray(c, dtype=float)
+    n = ev.shape[0]
+    xh = np.zeros((n, n))
+    xs = np.zeros((n, n))
+    if ev_bar is not None:
+        eb = np.asarray(ev_bar, dtype=float)
+        xh[np.arange(n), np.arange(n)] += eb
+        xs[np.arange(n), np.arange(n)] -= eb * ev
+    if c_bar is not None:
+        cb = np.asarray(c_bar, dtype=float)
+        k = cb.shape[1]
+        a = c.T @ cb
+        d = ev[None, :k] - ev[:, None]
+        fm = np.zeros((n, k))
+        ok = np.abs(d) >= guard
+        fm[ok] = 1.0 / d[ok]
+        fa = fm * a
+        xh[:, :k] += fa
+        xs[:, :k] -= fa * ev[None, :k]
+        xs[np.arange(k), np.arange(k)] -= 0.5 * a[np.arange(k), np.arange(k)]
+    hb = c @ (0.5 * (xh + xh.T)) @ c.T
+    sb = c @ (0.5 * (xs + xs.T)) @ c.T
+    return hb, sb
