@@ -157,6 +157,38 @@ int elsi_get_refine_info(elsi_handle h, int *iters, double *orth_err);
 int elsi_density_noalloc(int n_basis, int n_state, const double *evec, const double *occ,
                          const double *eval, double *den_mat, double *edm, void *stream);
 
+/* -kT S_ent of the last elsi_dm_real / elsi_dm_complex call (host scalar, <= 0): the
+ * entropy term of the free energy F = E_band - kT S_ent that is stationary in the
+ * occupations at fixed electron count, S_ent = -g sum_l [phi ln phi + (1-phi) ln(1-phi)]
+ * (phi = f_l / g) for Fermi-Dirac, g sum_l exp(-x_l^2) / (2 sqrt(pi)) (x_l =
+ * (eps_l - mu) / kT) for Gaussian broadening, 0 for integer occupation. The paper names
+ * the schemes (sec. 4.4) but no entropy; this is the term for which dF/dH = P. */
+int elsi_get_entropy(elsi_handle h, double *ts);
+
+/* ---- Reverse-mode derivatives (no counterpart in the paper) ------------------------
+ * elsi_dm_adjoint_real: for a loss L with dL/dF = f_bar, F = E_band - kT S_ent of a
+ * density-matrix solve: ham_bar = f_bar P, ovlp_bar = -f_bar W (dF/dH = P, dF/dS = -W;
+ * Hellmann-Feynman and Pulay terms). den_mat, edm: device n x n (P and W of that solve);
+ * ham_bar, ovlp_bar: device n x n outputs (ovlp_bar may be NULL). */
+int elsi_dm_adjoint_real(elsi_handle h, int n, double f_bar, const double *den_mat,
+                         const double *edm, double *ham_bar, double *ovlp_bar);
+
+/* elsi_ev_adjoint_real: reverse-mode derivative of H C = S C diag(eval), C^T S C = I.
+ * eval: device, all n eigenvalues ascending; evec: device n x n, ALL n S-orthonormal
+ * eigenvectors (column-major; the coupling to every other eigenvector enters the
+ * eigenvector derivative). eval_bar: device, n values dL/d eval (may be NULL);
+ * evec_bar: device n x k, dL/d evec[:, 0:k] (may be NULL), 0 <= k <= n.
+ * Outputs (device n x n, symmetric: the gradient with respect to a symmetric matrix):
+ * ham_bar = dL/dH = C sym(X_H) C^T, ovlp_bar = dL/dS = C sym(X_S) C^T (may be NULL) with,
+ * for A = C^T evec_bar and F_ij = 1/(eval_j - eval_i) (set to 0 where
+ * |eval_i - eval_j| < 1e-10, the degeneracy guard),
+ *   X_H = diag(eval_bar) + [F o A | 0],
+ *   X_S = -diag(eval_bar eval) - [(F o A) diag(eval_0..k-1) | 0] - diag(A_jj / 2).
+ * Errors: ELSI_ERR_ARG, ELSI_ERR_NOMEM, ELSI_ERR_CUDA. */
+int elsi_ev_adjoint_real(elsi_handle h, int n, int k, const double *eval, const double *evec,
+                         const double *eval_bar, const double *evec_bar, double *ham_bar,
+                         double *ovlp_bar);
+
 /* ---- Several problems: k-points and spin channels ----------------------------------
  * Sec. 2 (SINGLE_PROC mode): one process solves a group of k-points one after another;
  * sec. 4.4: the chemical potential's electron count is summed over k-points, spin

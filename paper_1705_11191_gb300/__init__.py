@@ -80,6 +80,9 @@ def _declare(lib):
         "elsi_batch_ev_complex": ([H, i, _ip, _ip, _pp, _pp, _vp], i),
         "elsi_occupation_weighted": ([H, i, _vp, _vp, d, _vp, _dp], i),
         "elsi_batch_dm": ([H, _vp, _pp, _pp, _dp], i),
+        "elsi_get_entropy": ([H, _dp], i),
+        "elsi_dm_adjoint_real": ([H, i, d, _vp, _vp, _vp, _vp], i),
+        "elsi_ev_adjoint_real": ([H, i, i, _vp, _vp, _vp, _vp, _vp, _vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -298,6 +301,41 @@ class Handle:
                                          _vp(hp(edm)), ctypes.byref(e))
         self._check(rc, "elsi_dm_real_host")
         return e.value
+
+    def get_entropy(self) -> float:
+        """-kT S_ent of the last density-matrix solve (F = E_band + this)."""
+        ts = ctypes.c_double(0.0)
+        self._check(self._lib.elsi_get_entropy(self._h, ctypes.byref(ts)), "elsi_get_entropy")
+        return ts.value
+
+    def dm_adjoint(self, f_bar: float, P, W):
+        """(dL/dH, dL/dS) = (f_bar P, -f_bar W) for dL/dF = f_bar."""
+        import torch
+        n = P.shape[0]
+        hb = torch.empty_like(P)
+        sb = torch.empty_like(P)
+        rc = self._lib.elsi_dm_adjoint_real(self._h, n, float(f_bar), _vp(_ptr(P)), _vp(_ptr(W)),
+                                            _vp(_ptr(hb)), _vp(_ptr(sb)))
+        self._check(rc, "elsi_dm_adjoint_real")
+        return hb, sb
+
+    def ev_adjoint(self, ev, C, ev_bar=None, C_bar=None):
+        """(dL/dH, dL/dS) for dL/d ev = ev_bar (n) and dL/dC[:, :k] = C_bar (n, k); C holds
+        all n eigenvectors as columns (n, n)."""
+        import torch
+        n = ev.shape[0]
+        ct = C.t().contiguous()  # column-major storage of C
+        gb = C_bar.t().contiguous() if C_bar is not None else None
+        k = 0 if C_bar is None else C_bar.shape[1]
+        hb = torch.empty((n, n), dtype=torch.float64, device=ev.device)
+        sb = torch.empty((n, n), dtype=torch.float64, device=ev.device)
+        eb = ev_bar.contiguous() if ev_bar is not None else None
+        rc = self._lib.elsi_ev_adjoint_real(self._h, n, k, _vp(_ptr(ev)), _vp(_ptr(ct)),
+                                            _vp(_ptr(eb) if eb is not None else None),
+                                            _vp(_ptr(gb) if gb is not None else None),
+                                            _vp(_ptr(hb)), _vp(_ptr(sb)))
+        self._check(rc, "elsi_ev_adjoint_real")
+        return hb, sb
 
     # ---- several problems (k-points / spin channels) ----
     def _batch_inputs(self, hams, ovlps, n_states):

@@ -180,6 +180,7 @@ int solve_complex(elsi_gb_handle_s *h, const double *ham, const double *ovlp, do
         if (energy) *energy = 0.5 * c->energy;
         h->mu = c->mu;
         h->energy = 0.5 * c->energy;
+        h->entropy = 0.5 * c->entropy;
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) return set_error(h, ELSI_ERR_CUDA, "complex fold");
     h->refine_iters = c->refine_iters;

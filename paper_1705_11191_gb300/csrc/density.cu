@@ -15,6 +15,17 @@ __device__ __forceinline__ double occ_phi(int scheme, double x)
     return 1.0 / (1.0 + exp(x));
 }
 
+// Per-state entropy summand s with -kT S_ent = kT g sum s, the term that makes the free
+// energy E_band - kT S_ent stationary in the occupations at fixed electron count:
+// Fermi-Dirac s = phi ln phi + (1 - phi) ln(1 - phi) (phi = f / g);
+// Gaussian s = -exp(-x^2) / (2 sqrt(pi)) (x = (eps - mu) / kT).
+__device__ __forceinline__ double occ_entropy(int scheme, double phi, double x)
+{
+    if (scheme == ELSI_OCC_GAUSSIAN) return -exp(-x * x) * 0.28209479177387814347;  // 1 / (2 sqrt(pi))
+    if (!(phi > 0.0 && phi < 1.0)) return 0.0;
+    return phi * log(phi) + (1.0 - phi) * log1p(-phi);
+}
+
 // One CTA. Spin factor g = 2. scheme 0: aufbau filling; 1/2: bisection on mu with the
 // exact-charge correction of sec. 4.4 when occ_accuracy is not reached.
 // stride 2 ("pairs"): states 2i and 2i+1 are the two real forms of one complex state;
@@ -44,6 +55,7 @@ __global__ void occupation_kernel(int k, const double *eps_all, double n_el_all,
             if (top > kk - 1) top = kk - 1;
             out[0] = eps(top);
             out[1] = stride * es;
+            out[2] = 0.0;
         }
     } else {
         auto count = [&](double mu) {
@@ -76,10 +88,14 @@ __global__ void occupation_kernel(int k, const double *eps_all, double n_el_all,
             }
         }
         __syncthreads();
-        double es = 0.0;
-        for (int l = tid; l < kk; l += nt) es += f[(size_t)l * stride] * eps(l);
+        double es = 0.0, ts = 0.0;
+        for (int l = tid; l < kk; l += nt) {
+            es += f[(size_t)l * stride] * eps(l);
+            ts += occ_entropy(scheme, f[(size_t)l * stride] / g, (eps(l) - mu) / kt);
+        }
         es = block_sum(es, red);
-        if (tid == 0) { out[0] = mu; out[1] = stride * es; }
+        ts = block_sum(ts, red);
+        if (tid == 0) { out[0] = mu; out[1] = stride * es; out[2] = stride * kt * g * ts; }
     }
     __syncthreads();
     if (stride > 1)
@@ -247,10 +263,14 @@ __global__ void occupation_weighted_kernel(int m, const double *eps, const doubl
         }
     }
     __syncthreads();
-    double es = 0.0;
-    for (int j = tid; j < m; j += nt) es += wt[j] * f[j] * eps[j];
+    double es = 0.0, ts = 0.0;
+    for (int j = tid; j < m; j += nt) {
+        es += wt[j] * f[j] * eps[j];
+        if (scheme != ELSI_OCC_INTEGER) ts += wt[j] * occ_entropy(scheme, f[j] / g, (eps[j] - mu) / kt);
+    }
     es = block_sum(es, red);
-    if (tid == 0) { out[0] = mu; out[1] = es; }
+    ts = block_sum(ts, red);
+    if (tid == 0) { out[0] = mu; out[1] = es; out[2] = kt * g * ts; }
 }
 
 cudaError_t occupation_weighted(cudaStream_t st, int m, const double *eps, const double *wt,

@@ -221,6 +221,34 @@ int elsi_get_edm_complex(elsi_handle h, double *edm)
     return get_edm_complex(h, edm);
 }
 
+int elsi_get_entropy(elsi_handle h, double *ts)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!ts) return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    if (!h->have_occ && !h->have_cedm) return set_error(h, ELSI_ERR_STATE, "no density-matrix solve yet");
+    *ts = h->entropy;
+    return ELSI_OK;
+}
+
+int elsi_dm_adjoint_real(elsi_handle h, int n, double f_bar, const double *den_mat,
+                         const double *edm, double *ham_bar, double *ovlp_bar)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (n < 1 || !den_mat || !ham_bar || (ovlp_bar && !edm))
+        return set_error(h, ELSI_ERR_ARG, "n < 1 or null pointer argument");
+    return dm_adjoint(h, n, f_bar, den_mat, edm, ham_bar, ovlp_bar);
+}
+
+int elsi_ev_adjoint_real(elsi_handle h, int n, int k, const double *eval, const double *evec,
+                         const double *eval_bar, const double *evec_bar, double *ham_bar,
+                         double *ovlp_bar)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (n < 1 || k < 0 || k > n || !eval || !evec || !ham_bar || (k > 0 && !evec_bar))
+        return set_error(h, ELSI_ERR_ARG, "bad size or null pointer argument");
+    return ev_adjoint(h, n, evec_bar ? k : 0, eval, evec, eval_bar, evec_bar, ham_bar, ovlp_bar);
+}
+
 int elsi_dm_batched_real(elsi_handle h, int nprob, const int *n_basis, const int *n_state,
                          const double *const *ham, const double *const *ovlp,
                          const double *weight, const double *n_electron, int shared_mu,

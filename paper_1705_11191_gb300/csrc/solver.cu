@@ -15,7 +15,7 @@ void free_workspace(elsi_gb_handle_s *h)
     Workspace &w = h->wk;
     void *bufs[] = {w.a, w.l, w.v1, w.edm, w.v2, w.tau2, w.band, w.t1, w.invd, w.work, w.z,
                     w.d, w.e, w.w, w.f, w.scal, w.stein, w.rf, w.oz, w.ozexp, w.q2f, w.sync, w.status,
-                    w.host_h, w.host_s, w.host_p};
+                    w.host_h, w.host_s, w.host_p, w.adj};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (w.status_host) cudaFreeHost(w.status_host);
@@ -238,6 +238,7 @@ int run_solve(elsi_gb_handle_s *h, const SolveRequest &rq)
     if (!ev_mode) {
         h->mu = w.scal_host[0];
         h->energy = w.scal_host[1];
+        h->entropy = w.scal_host[2];
         h->have_occ = true;
         h->have_edm = rq.want_edm;
     } else {

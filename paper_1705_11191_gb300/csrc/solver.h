@@ -49,6 +49,7 @@ struct Workspace {
     EGB_BUF(double, host_s)
     EGB_BUF(double, host_p)
     EGB_BUF(double, rfc)     // complex route: real eigenpair staging
+    EGB_BUF(double, adj)     // eigenpair adjoint scratch
 #undef EGB_BUF
     int *status_host = nullptr;  // pinned
     double *scal_host = nullptr; // pinned
@@ -81,6 +82,7 @@ struct elsi_gb_handle_s {
     int have_l_prec = -1;
     bool have_edm = false, have_occ = false;
     double mu = 0.0, energy = 0.0;
+    double entropy = 0.0;  // -kT S_ent of the last dm call
     int refine_iters = 0;
     double orth_err = 0.0;
     float stage_ms[egb::kNumStages] = {};
@@ -113,6 +115,10 @@ int solve_complex(elsi_gb_handle_s *h, const double *ham, const double *ovlp, do
 int get_edm_complex(elsi_gb_handle_s *h, double *edm);
 void free_complex(elsi_gb_handle_s *h);
 void free_batch(elsi_gb_handle_s *h);
+int dm_adjoint(elsi_gb_handle_s *h, int n, double fb, const double *p, const double *w,
+               double *hb, double *sb);
+int ev_adjoint(elsi_gb_handle_s *h, int n, int k, const double *eps, const double *c,
+               const double *eb, const double *g, double *hb, double *sb);
 int batch_ev(elsi_gb_handle_s *h, int nprob, const int *n_basis, const int *n_state,
              const double *const *ham, const double *const *ovlp, bool cplx, double *eval);
 int batch_occupation(elsi_gb_handle_s *h, int m, const double *eps, const double *wt, double n_el,
