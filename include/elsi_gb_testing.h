@@ -1,0 +1,33 @@
+/*
+ * Internal kernels of libelsi_gb exposed for their own tests (not part of the solver
+ * interface of arXiv:1705.11191; no counterpart in the paper).
+ *
+ * elsi_gb_gemm_f32: the binary32 GEMM of the reduction and back-transformations,
+ *   C (m x n, column-major, ldc) = alpha * op(A) op(B) + beta * C,
+ *   op(A) m x k (ta = 0: A column-major m x k, lda; ta = 1: A is k x m), op(B) k x n
+ *   (tb likewise), on the tcgen05 tensor cores as three TF32 products of hi/lo splits.
+ *   uplo = 1 writes only the lower triangle (row >= column) of C. All pointers are
+ *   device pointers; work: device scratch of elsi_gb_gemm_f32_work(m, n, k) floats
+ *   (16-byte aligned); status: device int[8], zeroed by the caller, receives
+ *   ELSI_ERR_TIMEOUT if a pipeline wait expired. Enqueued on stream (cudaStream_t, may
+ *   be NULL); returns 0, ELSI_ERR_ARG for bad sizes or scratch, ELSI_ERR_CUDA.
+ */
+#ifndef ELSI_GB_TESTING_H
+#define ELSI_GB_TESTING_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+size_t elsi_gb_gemm_f32_work(int m, int n, int k);
+int elsi_gb_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const float *A, int lda,
+                     const float *B, int ldb, float beta, float *C, int ldc, int uplo,
+                     float *work, size_t work_elems, int *status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELSI_GB_TESTING_H */

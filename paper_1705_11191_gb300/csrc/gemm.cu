@@ -102,11 +102,40 @@ template <typename T> struct GemmCfg;
 template <> struct GemmCfg<double> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
 template <> struct GemmCfg<float> { static constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8; };
 
+// Scratch for the tensor-core binary32 GEMM of the calling thread's current solve (set by
+// the solver around a binary32-route solve; absent elsewhere).
+static thread_local float *t_tc_work = nullptr;
+static thread_local size_t t_tc_elems = 0;
+static thread_local int *t_tc_status = nullptr;
+
+void set_tc_scratch(float *work, size_t elems, int *status)
+{
+    t_tc_work = work;
+    t_tc_elems = elems;
+    t_tc_status = status;
+}
+
+bool tc_scratch(float **work, size_t *elems, int **status)
+{
+    *work = t_tc_work;
+    *elems = t_tc_elems;
+    *status = t_tc_status;
+    return t_tc_work != nullptr;
+}
+
 template <typename T>
 cudaError_t gemm(cudaStream_t st, int ta, int tb, int m, int n, int k, T alpha, const T *A,
                  int lda, const T *B, int ldb, T beta, T *C, int ldc, int uplo)
 {
     if (m <= 0 || n <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        // binary32 products large enough for the tensor-core path
+        if (t_tc_work && k >= 16 && (double)m * n * k >= 4.0e6) {
+            cudaError_t e = tc_gemm_f32(st, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                                        uplo, t_tc_work, t_tc_elems, t_tc_status);
+            if (e != cudaErrorNotSupported) return e;
+        }
+    }
     using G = GemmCfg<T>;
     dim3 grid(ceil_div(m, G::BM), ceil_div(n, G::BN));
     dim3 block((G::BM / G::TM) * (G::BN / G::TN));
@@ -135,6 +164,13 @@ cudaError_t gemm_splitk(cudaStream_t st, int ta, int tb, int m, int n, int k, T 
                         size_t part_elems)
 {
     if (m <= 0 || n <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        if (t_tc_work && k >= 16 && (double)m * n * k >= 4.0e6) {
+            cudaError_t e = tc_gemm_f32(st, ta, tb, m, n, k, alpha, A, lda, B, ldb, 0.0f, C, ldc, 0,
+                                        t_tc_work, t_tc_elems, t_tc_status);
+            if (e != cudaErrorNotSupported) return e;
+        }
+    }
     using G = GemmCfg<T>;
     const int tiles = ceil_div(m, G::BM) * ceil_div(n, G::BN);
     int splits = ceil_div(2 * 152, tiles);

@@ -16,6 +16,29 @@ cudaError_t gemm(cudaStream_t st, int ta, int tb, int m, int n, int k, T alpha,
                  const T *A, int lda, const T *B, int ldb, T beta, T *C, int ldc,
                  int uplo = 0);
 
+// Binary32-accuracy GEMM on the tcgen05 tensor cores (three TF32 products of hi/lo splits;
+// tc_gemm.cu). work: tc_gemm_work_elems(m, n, k) floats, 16-byte aligned. Returns
+// cudaErrorNotSupported when it cannot run (scratch too small, no tensor-map encoder).
+size_t tc_gemm_work_elems(int m, int n, int k);
+// Sum of products over K pieces: C = alpha * sum_i op(A_i) op(B_i) + beta * C, piece i of
+// width k (the same for A_i and B_i), op(A_i) m x k (trans = 0: p[r + q ld], 1: p[q + r ld]),
+// op(B_i) k x n (trans = 0: p[q + c ld], 1: p[c + q ld]).
+struct TcPart {
+    const float *p;
+    int ld, trans, k;
+};
+cudaError_t tc_gemm_f32_parts(cudaStream_t st, int m, int n, int nparts, const TcPart *a,
+                              const TcPart *b, float alpha, float beta, float *C, int ldc, int uplo,
+                              float *work, size_t work_elems, int *status);
+// Scratch of this thread's current solve for the tensor-core path (nullptr if none).
+bool tc_scratch(float **work, size_t *elems, int **status);
+// Routes this thread's binary32 gemm() calls with large enough shapes to tc_gemm_f32 with
+// the given scratch (work = nullptr: SIMT kernel only).
+void set_tc_scratch(float *work, size_t elems, int *status);
+cudaError_t tc_gemm_f32(cudaStream_t st, int ta, int tb, int m, int n, int k, float alpha,
+                        const float *A, int lda, const float *B, int ldb, float beta, float *C,
+                        int ldc, int uplo, float *work, size_t work_elems, int *status);
+
 // C = alpha * op(A) * op(B) with K split over several CTAs (for small outputs with a long
 // K); part: scratch of part_elems elements for the partial products.
 template <typename T>

@@ -15,7 +15,7 @@ void free_workspace(elsi_gb_handle_s *h)
     Workspace &w = h->wk;
     void *bufs[] = {w.a, w.l, w.v1, w.edm, w.v2, w.tau2, w.band, w.t1, w.invd, w.work, w.z,
                     w.d, w.e, w.w, w.f, w.scal, w.stein, w.rf, w.oz, w.ozexp, w.q2f, w.sync, w.status,
-                    w.host_h, w.host_s, w.host_p, w.adj};
+                    w.host_h, w.host_s, w.host_p, w.adj, w.tcw};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (w.status_host) cudaFreeHost(w.status_host);
@@ -70,6 +70,7 @@ static int ensure_workspace(elsi_gb_handle_s *h, int kz)
                                       3 * ozaki_split_elems((int)n, (int)k));
         ENSURE(ozexp, int, 8 * (n + k + 256));
         ENSURE(q2f, float, q2_tfactor_elems((int)n, b));
+        ENSURE(tcw, float, tc_gemm_work_elems((int)n, (int)n, (int)n));
     }
     if (!w.status_host && cudaMallocHost((void **)&w.status_host, sizeof(int) * ST_WORDS) != cudaSuccess)
         return set_error(h, ELSI_ERR_NOMEM, "pinned status");
@@ -194,7 +195,9 @@ int run_solve(elsi_gb_handle_s *h, const SolveRequest &rq)
     if (h->precision == ELSI_PREC_FP64) {
         rc = solve_fp64(h, rq);
     } else {
+        set_tc_scratch(w.tcw, w.tcw_cap / sizeof(float), w.status);
         rc = solve_fp32_refine(h, rq);
+        set_tc_scratch(nullptr, 0, nullptr);
         if (rc == ELSI_ERR_NO_CONVERGENCE) {
             // The binary32 start was too far from the solution for the refinement (e.g. a
             // badly conditioned S): solve the same problem along the binary64 route.

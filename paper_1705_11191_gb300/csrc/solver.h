@@ -43,6 +43,7 @@ struct Workspace {
     EGB_BUF(__nv_bfloat16, oz)  // digit planes of the binary64-accurate products
     EGB_BUF(int, ozexp)      // their exponents
     EGB_BUF(float, q2f)      // compact-WY factors of Q2 (binary32 route)
+    EGB_BUF(float, tcw)      // TF32 hi/lo operand planes of the tensor-core GEMM
     EGB_BUF(unsigned, sync)  // grid-barrier words + partial sums
     EGB_BUF(int, status)
     EGB_BUF(double, host_h)  // staging for the _host entry points
@@ -73,7 +74,7 @@ struct elsi_gb_handle_s {
     int mu_max_steps = 200;
     int precision = ELSI_PREC_FP64;
     int band_width = 64;
-    int refine_max_iter = 3;
+    int refine_max_iter = 4;
     bool reuse_l = false;
     cudaStream_t stream = nullptr;
     int occ_stride = 1;  // 2 in the real form of a complex problem (pairs of states)

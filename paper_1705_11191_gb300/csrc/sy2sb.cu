@@ -261,9 +261,27 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         // W = X - 1/2 V Z
         if ((e = cudaMemcpyAsync(W, X, sizeof(T) * (size_t)m * bw, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
         if ((e = gemm<T>(st, 0, 0, m, bw, bw, T(-0.5), V, n, Z, bw, T(1), W, m)) != cudaSuccess) return e;
-        // A22 -= V W^T + W V^T   (lower triangle), then mirror
-        if ((e = gemm<T>(st, 0, 1, m, m, bw, T(-1), V, n, W, m, T(1), A22, lda, 1)) != cudaSuccess) return e;
-        if ((e = gemm<T>(st, 0, 1, m, m, bw, T(-1), W, m, V, n, T(1), A22, lda, 1)) != cudaSuccess) return e;
+        // A22 -= V W^T + W V^T   (lower triangle), then mirror. On the tensor-core path the
+        // two products are one GEMM over K = 2 bw: [V W] [W V]^T.
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+            float *tw;
+            size_t te;
+            int *ts;
+            if (tc_scratch(&tw, &te, &ts)) {
+                TcPart pa[2] = {{(const float *)V, n, 0, bw}, {(const float *)W, m, 0, bw}};
+                TcPart pb[2] = {{(const float *)W, m, 1, bw}, {(const float *)V, n, 1, bw}};
+                e = tc_gemm_f32_parts(st, m, m, 2, pa, pb, -1.0f, 1.0f, (float *)A22, lda, 1, tw, te, ts);
+                if (e != cudaErrorNotSupported) {
+                    if (e != cudaSuccess) return e;
+                    done = true;
+                }
+            }
+        }
+        if (!done) {
+            if ((e = gemm<T>(st, 0, 1, m, m, bw, T(-1), V, n, W, m, T(1), A22, lda, 1)) != cudaSuccess) return e;
+            if ((e = gemm<T>(st, 0, 1, m, m, bw, T(-1), W, m, V, n, T(1), A22, lda, 1)) != cudaSuccess) return e;
+        }
         if ((e = mirror_lower<T>(st, m, A22, lda)) != cudaSuccess) return e;
     }
     (void)work_elems;

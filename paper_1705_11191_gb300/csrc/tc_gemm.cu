@@ -1,0 +1,481 @@
+// Binary32-accuracy GEMM on the 5th-generation tensor cores (tcgen05, sm_103a):
+//   C (m x n, column-major, ldc) = alpha * op(A) op(B) + beta * C.
+// Each operand x is split into two TF32 planes, x = hi + lo (hi = tf32(x), lo = tf32(x - hi)),
+// and the product is accumulated in FP32 as A_hi B_hi + A_hi B_lo + A_lo B_hi (the A_lo B_lo
+// term is below binary32 rounding). This is the binary32 GEMM of the reduction and the
+// back-transformations of the binary32 route.
+//
+// Structure of one CTA (192 threads, one 128 x 128 tile of C):
+//   warp 0, one lane : TMA producer. Loads the K-major hi and lo tiles of A and B (32 fp32 of
+//                      K = 128 bytes per row, 128-byte swizzle) into a 3-stage ring, one
+//                      mbarrier per stage with the transaction byte count;
+//   warp 1, one lane : MMA issuer. tcgen05.mma kind::tf32, M = 128, N = 128, K = 8 per
+//                      instruction, accumulator in tensor memory (128 lanes x 128 columns);
+//                      tcgen05.commit frees a stage when its MMAs have read it;
+//   warps 2-5        : epilogue: sum the K chunks of the two tensor-memory accumulators
+//                      (tcgen05.ld, 32 rows per warp) in registers, then C = alpha acc +
+//                      beta C with coalesced column-major stores; warp 2 allocates and
+//                      frees the tensor memory.
+// Every wait is bounded; on expiry the kernel records ELSI_ERR_TIMEOUT and finishes without
+// further waits on the pipeline (after a bounded wait for its own TMA copies in flight).
+#include <cuda.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace egb {
+namespace tcg {
+
+constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3;
+constexpr int CH = 2;  // k-tiles per tensor-memory accumulation chunk (K = 64)
+constexpr int TILE_BYTES = BM * BK * 4;  // 16 KB (BN == BM)
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TMEM_COLS = 4 * BN;  // two buffers x (hi*hi sum, cross-term sum)
+constexpr long long kWaitLimit = 1ll << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on the phase with the given parity; false on expiry.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+{
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if (i > 32) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, unsigned bar,
+                                            int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of 128 bytes,
+// 8-row groups 1024 bytes apart (SBO); LBO unused for this layout.
+__device__ __forceinline__ unsigned long long sdesc(unsigned saddr)
+{
+    unsigned long long d = 0;
+    d |= (unsigned long long)((saddr >> 4) & 0x3FFFu);
+    d |= (unsigned long long)1 << 16;
+    d |= (unsigned long long)(1024 >> 4) << 32;
+    d |= (unsigned long long)1 << 46;  // descriptor version of sm_100 family
+    d |= (unsigned long long)2 << 61;  // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::tf32, FP32 accumulator, A and B K-major, M = 128, N = BN.
+__host__ __device__ constexpr unsigned idesc_tf32()
+{
+    return (1u << 4)                  // D format F32
+           | (2u << 7)                // A format TF32
+           | (2u << 10)               // B format TF32
+           | ((unsigned)(BN >> 3) << 17)
+           | ((unsigned)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(unsigned tmem_d, unsigned long long a, unsigned long long b,
+                                         unsigned idesc, unsigned accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive accumulator columns of this thread's lane (row).
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float *v)
+{
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct Maps {
+    CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Warps: 0 = TMA producer (one lane), 1 = MMA issuer (one lane), 2..5 = epilogue (warp w
+// reads tensor-memory lanes 32 (w mod 4) .. + 31, i.e. those rows of the tile). K is
+// accumulated in chunks of CH k-tiles in one of two tensor-memory buffers, each holding the
+// hi*hi sum and the (2^-11 times smaller) cross-term sum separately; the epilogue warps add
+// each chunk into binary32 registers (round to nearest) while the MMA issuer fills the other
+// buffer. The tensor-memory accumulation is not rounded to nearest, so its error grows with
+// the number of MMAs summed into one accumulator and with that accumulator's magnitude;
+// short chunks and the separate small sum keep it at the binary32 level.
+__global__ void __launch_bounds__(192, 1)
+gemm_tf32x3_kernel(const __grid_constant__ Maps maps, int m, int n, int kp, float alpha,
+                   float beta, float *__restrict__ C, int ldc, int uplo, int *status)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((size_t)smem_raw + 1023) & ~(size_t)1023);
+    unsigned long long *bars = (unsigned long long *)(smem + STAGES * STAGE_BYTES);
+    // bars: [0,S) full, [S,2S) empty, 2S+b accumulator b full, 2S+2+b accumulator b empty
+    unsigned *tmem_slot = (unsigned *)(bars + 2 * STAGES + 4);
+    __shared__ int aborted;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    if (uplo && m0 + BM - 1 < n0) return;  // tile strictly above the diagonal
+    const int nk = kp / BK;
+    const int nchunk = (nk + CH - 1) / CH;
+    const unsigned full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
+    const unsigned accf0 = smem_u32(&bars[2 * STAGES]), acce0 = smem_u32(&bars[2 * STAGES + 2]);
+
+    if (tid == 0) {
+        for (int s = 0; s < 2 * STAGES + 2; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        mbar_init(acce0, 4);
+        mbar_init(acce0 + 8, 4);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        aborted = 0;
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+
+    int armed = 0;  // producer: stages loaded
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % STAGES;
+                const unsigned ph = (kt / STAGES) & 1;
+                if (kt >= STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1)) {
+                    report_error(status, ELSI_ERR_TIMEOUT, 1);
+                    atomicExch(&aborted, 1);
+                    break;
+                }
+                if (*(volatile int *)&aborted) break;
+                unsigned char *st = smem + s * STAGE_BYTES;
+                const unsigned full = full0 + 8 * s;
+                mbar_expect_tx(full, STAGE_BYTES);
+                tma_load_2d(smem_u32(st), &maps.a_hi, full, kt * BK, m0);
+                tma_load_2d(smem_u32(st + TILE_BYTES), &maps.a_lo, full, kt * BK, m0);
+                tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &maps.b_hi, full, kt * BK, n0);
+                tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &maps.b_lo, full, kt * BK, n0);
+                armed = kt + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const unsigned idesc = idesc_tf32();
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % STAGES, g = kt / CH, bsel = g & 1;
+                const unsigned ph = (kt / STAGES) & 1;
+                const bool first = (kt % CH) == 0;
+                if (first && g >= 2 && !mbar_wait(acce0 + 8 * bsel, ((g >> 1) - 1) & 1)) {
+                    report_error(status, ELSI_ERR_TIMEOUT, 4);
+                    atomicExch(&aborted, 1);
+                    break;
+                }
+                if (!mbar_wait(full0 + 8 * s, ph)) {
+                    report_error(status, ELSI_ERR_TIMEOUT, 2);
+                    atomicExch(&aborted, 1);
+                    break;
+                }
+                tc_fence_after();
+                const unsigned base = smem_u32(smem + s * STAGE_BYTES);
+                const unsigned d = tmem + bsel * 2 * BN;  // hi*hi sum; cross terms at + BN
+#pragma unroll
+                for (int kk = 0; kk < BK / 8; ++kk) {
+                    const unsigned off = kk * 32;  // 8 tf32 = 32 bytes along K
+                    const unsigned long long ah = sdesc(base + off), al = sdesc(base + TILE_BYTES + off);
+                    const unsigned long long bh = sdesc(base + 2 * TILE_BYTES + off);
+                    const unsigned long long bl = sdesc(base + 3 * TILE_BYTES + off);
+                    const unsigned acc = (first && kk == 0) ? 0u : 1u;
+                    mma_tf32(d + BN, al, bh, idesc, acc);
+                    mma_tf32(d + BN, ah, bl, idesc, 1u);
+                    mma_tf32(d, ah, bh, idesc, acc);
+                }
+                mma_commit(empty0 + 8 * s);
+                if ((kt % CH) == CH - 1 || kt == nk - 1) mma_commit(accf0 + 8 * bsel);
+            }
+        }
+    } else {
+        const int quarter = warp & 3;
+        float acc[BN];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) acc[j] = 0.0f;
+        bool ok = true;
+        for (int g = 0; g < nchunk && ok; ++g) {
+            const int bsel = g & 1;
+            ok = mbar_wait(accf0 + 8 * bsel, (g >> 1) & 1);
+            if (!ok) {
+                if (lane == 0) {
+                    report_error(status, ELSI_ERR_TIMEOUT, 3);
+                    atomicExch(&aborted, 1);
+                }
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int q = 0; q < BN / 32; ++q) {
+                float v[32];
+                const unsigned ta = tmem + ((unsigned)(quarter * 32) << 16) + bsel * 2 * BN + q * 32;
+                tmem_ld32(ta + BN, v);  // cross terms
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[q * 32 + j] += v[j];
+                tmem_ld32(ta, v);  // hi * hi
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[q * 32 + j] += v[j];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * bsel);
+        }
+        const int row = m0 + quarter * 32 + lane;
+        if (ok && row < m) {
+            // 16 columns at a time: all loads of C first (independent, in flight together),
+            // then the stores; each column is one 128-byte line per warp.
+            float *crow = C + (size_t)row;
+#pragma unroll
+            for (int q = 0; q < BN / 16; ++q) {
+                float cv[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + q * 16 + j;
+                    const bool in = col < n && (!uplo || row >= col);
+                    cv[j] = (beta != 0.0f && in) ? crow[(size_t)col * ldc] : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + q * 16 + j;
+                    if (col < n && (!uplo || row >= col))
+                        crow[(size_t)col * ldc] = alpha * acc[q * 16 + j] + beta * cv[j];
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (aborted && warp == 0 && lane == 0) {
+        // bounded wait for this CTA's own TMA copies still in flight
+        for (int kt = (armed > STAGES ? armed - STAGES : 0); kt < armed; ++kt)
+            mbar_wait(full0 + 8 * (kt % STAGES), (kt / STAGES) & 1);
+    }
+    __syncthreads();
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
+}
+
+// Columns [q_off, q_off + kw) of the rows x kp plane (K-major) of hi / lo TF32 parts of the
+// operand piece element (r, q) = src[r * sr + q * sq] (one of sr, sq is 1), q < k, zero for
+// k <= q < kw. 32 x 32 tiles through shared memory so that reads and writes coalesce.
+__global__ void split_planes_kernel(int rows, int k, int kw, int kp, int q_off,
+                                    const float *__restrict__ src, long long sr, long long sq,
+                                    float *__restrict__ hi, float *__restrict__ lo)
+{
+    __shared__ float t[32][33];
+    const int r0 = blockIdx.y * 32, q0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    if (sq == 1) {
+        for (int i = ty; i < 32; i += 8) {
+            const int r = r0 + i, q = q0 + tx;
+            t[i][tx] = (r < rows && q < k) ? src[r * sr + q] : 0.0f;
+        }
+    } else {
+        for (int i = ty; i < 32; i += 8) {
+            const int q = q0 + i, r = r0 + tx;
+            t[tx][i] = (r < rows && q < k) ? src[r + q * sq] : 0.0f;
+        }
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int r = r0 + i, q = q0 + tx;
+        if (r < rows && q < kw) {
+            const float x = t[i][tx];
+            unsigned h;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+            h &= 0xFFFFE000u;
+            const float xh = __uint_as_float(h);
+            unsigned l;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - xh));
+            l &= 0xFFFFE000u;
+            hi[(size_t)r * kp + q_off + q] = xh;
+            lo[(size_t)r * kp + q_off + q] = __uint_as_float(l);
+        }
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// rows x kp fp32 plane, K-major, boxes of 32 (K) x 128 (rows), 128-byte swizzle.
+static bool make_map(CUtensorMap *map, const float *plane, int rows, int kp)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kp * sizeof(float)};
+    cuuint32_t box[2] = {BK, BM};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)plane, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tcg
+
+static inline int kround(int k) { return ((k + tcg::BK - 1) / tcg::BK) * tcg::BK; }
+
+size_t tc_gemm_work_elems(int m, int n, int k)
+{
+    return 2 * ((size_t)m + n) * (size_t)kround(k) + 64;
+}
+
+cudaError_t tc_gemm_f32_parts(cudaStream_t st, int m, int n, int nparts, const TcPart *a,
+                              const TcPart *b, float alpha, float beta, float *C, int ldc, int uplo,
+                              float *work, size_t work_elems, int *status)
+{
+    using namespace tcg;
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    int kp = 0;
+    for (int i = 0; i < nparts; ++i) {
+        if (a[i].k != b[i].k || a[i].k <= 0) return cudaErrorNotSupported;
+        kp += kround(a[i].k);
+    }
+    if (kp <= 0 || work_elems < 2 * ((size_t)m + n) * kp + 64 || ((size_t)work & 15))
+        return cudaErrorNotSupported;
+    float *ahi = work, *alo = ahi + (size_t)m * kp, *bhi = alo + (size_t)m * kp, *blo = bhi + (size_t)n * kp;
+    dim3 tb32(32, 8);
+    int off = 0;
+    for (int i = 0; i < nparts; ++i) {
+        const int kw = kround(a[i].k);
+        // op(A) element (i, q): trans = 0 -> A[i + q ld]; trans = 1 -> A[q + i ld]
+        EGB_COUNT_LAUNCH();
+        split_planes_kernel<<<dim3(kw / 32, (m + 31) / 32), tb32, 0, st>>>(
+            m, a[i].k, kw, kp, off, a[i].p, a[i].trans ? (long long)a[i].ld : 1,
+            a[i].trans ? 1 : (long long)a[i].ld, ahi, alo);
+        // op(B) element (q, j) is plane row j: trans = 0 -> B[q + j ld]; trans = 1 -> B[j + q ld]
+        EGB_COUNT_LAUNCH();
+        split_planes_kernel<<<dim3(kw / 32, (n + 31) / 32), tb32, 0, st>>>(
+            n, b[i].k, kw, kp, off, b[i].p, b[i].trans ? 1 : (long long)b[i].ld,
+            b[i].trans ? (long long)b[i].ld : 1, bhi, blo);
+        off += kw;
+    }
+    Maps maps;
+    if (!make_map(&maps.a_hi, ahi, m, kp) || !make_map(&maps.a_lo, alo, m, kp) ||
+        !make_map(&maps.b_hi, bhi, n, kp) || !make_map(&maps.b_lo, blo, n, kp))
+        return cudaErrorNotSupported;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        SMEM_BYTES);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN);
+    EGB_COUNT_LAUNCH();
+    gemm_tf32x3_kernel<<<grid, 192, SMEM_BYTES, st>>>(maps, m, n, kp, alpha, beta, C, ldc, uplo, status);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_f32(cudaStream_t st, int ta, int tb, int m, int n, int k, float alpha,
+                        const float *A, int lda, const float *B, int ldb, float beta, float *C,
+                        int ldc, int uplo, float *work, size_t work_elems, int *status)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    if (k <= 0) return cudaErrorNotSupported;
+    TcPart pa{A, lda, ta, k}, pb{B, ldb, tb, k};
+    return tc_gemm_f32_parts(st, m, n, 1, &pa, &pb, alpha, beta, C, ldc, uplo, work, work_elems, status);
+}
+
+}  // namespace egb
+
+extern "C" size_t elsi_gb_gemm_f32_work(int m, int n, int k)
+{
+    return egb::tc_gemm_work_elems(m, n, k);
+}
+
+extern "C" int elsi_gb_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const float *A,
+                                int lda, const float *B, int ldb, float beta, float *C, int ldc,
+                                int uplo, float *work, size_t work_elems, int *status, void *stream)
+{
+    if (m < 0 || n < 0 || k < 1 || !A || !B || !C || !work || !status) return ELSI_ERR_ARG;
+    cudaError_t e = egb::tc_gemm_f32((cudaStream_t)stream, ta, tb, m, n, k, alpha, A, lda, B, ldb,
+                                     beta, C, ldc, uplo, work, work_elems, status);
+    if (e == cudaErrorNotSupported) return ELSI_ERR_ARG;
+    return e == cudaSuccess ? ELSI_OK : ELSI_ERR_CUDA;
+}
