@@ -19,14 +19,13 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tcgen05.cuh"
 
 namespace egb {
 
 constexpr int kOzD = 7;         // digits per operand
 constexpr int kOzBits = 7;      // bits per digit
-constexpr int kOzBM = 128, kOzBN = 128, kOzBK = 16;
-constexpr int kOzStages = 3;
-constexpr int kOzChunkSteps = 16;  // k16 steps per exact binary32 chunk (256 along K)
+constexpr int kOzBM = 128, kOzBN = 128, kOzBK = 16;  // plane padding: rows, K
 
 // ------------------------------------------------------------------ splitting
 // Vector v (0 <= v < V) has elements x(v, q) = src[v * sv + q * sq], q < K. Writes
@@ -82,174 +81,211 @@ __global__ void ozaki_split_kernel(int V, int Vpad, int K, int Kpad, const doubl
     }
 }
 
-// ------------------------------------------------------------------ GEMM
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
+// ------------------------------------------------------------------ GEMM (tcgen05)
+// One CTA per 128 x 128 tile of C, 192 threads:
+//   warp 0, one lane: TMA producer of the (A digit plane, B digit plane) k-tiles, 64 bf16 of
+//                     K (128 bytes, 128-byte swizzle) x 128 rows each, into a STAGES ring;
+//   warp 1, one lane: MMA issuer, tcgen05.mma kind::f16 (bf16 x bf16 -> fp32), M = N = 128,
+//                     K = 16 per instruction;
+//   warps 2..5:       epilogue, warp w owns tensor-memory lanes (rows) 32 (w mod 4) .. + 31.
+// Work order: levels L = D+1 down to 2 (smallest contributions first), chunks of 256 along
+// K, pairs (s, L - s), k-tiles. Each chunk's sum over its pairs and k-tiles goes to one of
+// two tensor-memory accumulators: the products are integers and the sum stays below 2^24,
+// so the accumulation is exact whatever its rounding. The epilogue converts each chunk to
+// int32 and adds it in registers (exact); at the end of a level it adds
+// alpha 2^(e_i + f_j - 7L) times the level sum to C in binary64.
+namespace oztc {
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 5;
+constexpr int CHUNK_TILES = 256 / BK;         // k-tiles per exact chunk
+constexpr int TILE_BYTES = BM * BK * 2;       // 16 KB
+constexpr int STAGE_BYTES = 2 * TILE_BYTES;   // A tile + B tile
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TMEM_COLS = 2 * BN;
 
-__device__ __forceinline__ void cp_async16(unsigned dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-__device__ __forceinline__ void ldmatrix_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2,
-                                            unsigned &r3)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float *c, const unsigned *a, unsigned b0, unsigned b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// Shared tile: 128 rows x 16 bf16 (32 bytes = two 16-byte chunks per row). Chunk c of row
-// r is stored at chunk c ^ ((r >> 2) & 1): the 8 row addresses of every ldmatrix 8x8
-// matrix then hit distinct banks.
-__device__ __forceinline__ int tile_off(int r, int c) { return r * 32 + ((c ^ ((r >> 2) & 1)) << 4); }
-
-struct OzArgs {
-    int M, N, Kpad;                 // padded sizes: M, N multiples of 128, Kpad of 16
-    const __nv_bfloat16 *A;         // planes [D][M][Kpad]
-    size_t a_plane;
-    const int *ea;                  // M
-    const __nv_bfloat16 *B;         // planes [D][N][Kpad]
-    size_t b_plane;
-    const int *eb;                  // N
-    double alpha, beta;
-    double *C;                      // m_real x n_real, ldc
-    int ldc, m_real, n_real, uplo;
+struct Maps {
+    CUtensorMap a, b;  // planes as (D * Mpad) x Kpad and (D * Npad) x Kpad bf16 matrices
 };
 
-// C = alpha * A B + beta * C for the 128 x 128 tile of this CTA; 8 warps (2 x 4), warp tile
-// 64 x 32; one pass over K per level L.
-__global__ void __launch_bounds__(256) ozaki_gemm_kernel(OzArgs a)
+struct Args {
+    int m_real, n_real, kpad, mpad, npad, uplo, ldc;
+    const int *ea, *eb;
+    double alpha, beta;
+    double *C;
+    int *status;
+};
+}  // namespace oztc
+
+__global__ void __launch_bounds__(192, 1)
+ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a)
 {
-    extern __shared__ __align__(128) unsigned char sm[];
-    const int m0 = blockIdx.x * kOzBM, n0 = blockIdx.y * kOzBN;
-    if (m0 >= a.m_real || n0 >= a.n_real) return;
-    if (a.uplo == 1 && m0 + kOzBM - 1 < n0) return;
+    using namespace oztc;
+    using namespace tc5;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((size_t)smem_raw + 1023) & ~(size_t)1023);
+    unsigned long long *bars = (unsigned long long *)(smem + STAGES * STAGE_BYTES);
+    // bars: [0,S) full, [S,2S) empty, 2S+b accumulator b full, 2S+2+b accumulator b empty
+    unsigned *tmem_slot = (unsigned *)(bars + 2 * STAGES + 4);
+    __shared__ int aborted;
+
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
-    const int tile_bytes = kOzBM * kOzBK * 2;  // 4096
-    const int nks = a.Kpad / kOzBK;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    if (m0 >= a.m_real || n0 >= a.n_real) return;
+    if (a.uplo && m0 + BM - 1 < n0) return;  // tile strictly above the diagonal
+    const int nkt = (a.kpad + BK - 1) / BK;
+    const int nch = (nkt + CHUNK_TILES - 1) / CHUNK_TILES;
+    const unsigned full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
+    const unsigned accf0 = smem_u32(&bars[2 * STAGES]), acce0 = smem_u32(&bars[2 * STAGES + 2]);
 
-    for (int L = kOzD + 1; L >= 2; --L) {
-        const int s_lo = max(1, L - kOzD), s_hi = min(kOzD, L - 1);
-        const int np = s_hi - s_lo + 1;                 // pairs (s, L - s)
-        const int stage_bytes = 2 * np * tile_bytes;    // A planes s_lo..s_hi, B planes L-s_hi..L-s_lo
-        float acc[4][4][4];
-        int iacc[4][4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) { acc[i][j][q] = 0.f; iacc[i][j][q] = 0; }
-
-        auto load_stage = [&](int ks, int stage) {
-            unsigned base = smem_u32(sm) + stage * stage_bytes;
-            const int kq = ks * kOzBK;
-            // 2*np tiles x 128 rows x 2 chunks
-            const int chunks = 2 * np * kOzBM * 2;
-            for (int c = tid; c < chunks; c += 256) {
-                int tile = c / (kOzBM * 2);
-                int rem = c % (kOzBM * 2);
-                int r = rem >> 1, ch = rem & 1;
-                const __nv_bfloat16 *src;
-                if (tile < np) {
-                    int s = s_lo + tile;
-                    src = a.A + (size_t)(s - 1) * a.a_plane + (size_t)(m0 + r) * a.Kpad + kq + ch * 8;
-                } else {
-                    int s = s_lo + (tile - np);
-                    int t = L - s;
-                    src = a.B + (size_t)(t - 1) * a.b_plane + (size_t)(n0 + r) * a.Kpad + kq + ch * 8;
-                }
-                cp_async16(base + tile * tile_bytes + tile_off(r, ch), src);
-            }
-        };
-
-#pragma unroll
-        for (int st = 0; st < kOzStages - 1; ++st) {
-            if (st < nks) load_stage(st, st);
-            cp_async_commit();
-        }
-        for (int ks = 0; ks < nks; ++ks) {
-            cp_async_wait<kOzStages - 2>();
-            __syncthreads();
-            {
-                int nxt = ks + kOzStages - 1;
-                if (nxt < nks) load_stage(nxt, nxt % kOzStages);
-                cp_async_commit();
-            }
-            const unsigned base = smem_u32(sm) + (ks % kOzStages) * stage_bytes;
-            for (int p = 0; p < np; ++p) {
-                const unsigned at = base + p * tile_bytes;          // A plane s_lo + p
-                const unsigned bt = base + (np + p) * tile_bytes;   // B plane L - (s_lo + p)
-                unsigned af[4][4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    int r = wm + i * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
-                    int ch = lane >> 4;
-                    ldmatrix_x4(at + tile_off(r, ch), af[i][0], af[i][1], af[i][2], af[i][3]);
-                }
-                unsigned bf[4][2];
-#pragma unroll
-                for (int jj = 0; jj < 2; ++jj) {
-                    int r = wn + jj * 16 + (lane & 7) + (lane >> 4) * 8;
-                    int ch = (lane >> 3) & 1;
-                    unsigned r0, r1, r2, r3;
-                    ldmatrix_x4(bt + tile_off(r, ch), r0, r1, r2, r3);
-                    bf[jj * 2][0] = r0; bf[jj * 2][1] = r1;
-                    bf[jj * 2 + 1][0] = r2; bf[jj * 2 + 1][1] = r3;
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j][0], bf[j][1]);
-            }
-            if ((ks + 1) % kOzChunkSteps == 0 || ks == nks - 1) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            iacc[i][j][q] += __float2int_rn(acc[i][j][q]);
-                            acc[i][j][q] = 0.f;
-                        }
-            }
-        }
-        cp_async_wait<0>();
-        __syncthreads();
-        // level epilogue: C (+)= alpha 2^(e_i + f_j - 7L) iacc
-        const bool first = (L == kOzD + 1);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    int r = m0 + wm + i * 16 + (lane >> 2) + (q >> 1) * 8;
-                    int c = n0 + wn + j * 8 + (lane & 3) * 2 + (q & 1);
-                    if (r >= a.m_real || c >= a.n_real) continue;
-                    if (a.uplo == 1 && r < c) continue;
-                    double val = a.alpha * ldexp((double)iacc[i][j][q], a.ea[r] + a.eb[c] - kOzBits * L);
-                    double *cp = a.C + (size_t)r + (size_t)c * a.ldc;
-                    if (first) *cp = (a.beta == 0.0) ? val : fma(a.beta, *cp, val);
-                    else *cp += val;
-                }
+    if (tid == 0) {
+        for (int q = 0; q < 2 * STAGES + 2; ++q) mbar_init(smem_u32(&bars[q]), 1);
+        mbar_init(acce0, 4);
+        mbar_init(acce0 + 8, 4);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        aborted = 0;
     }
+    if (warp == 2) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *tmem_slot;
+
+    int armed = 0;
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            bool stop = false;
+            for (int L = kOzD + 1; L >= 2 && !stop; --L) {
+                const int s_lo = max(1, L - kOzD), s_hi = min(kOzD, L - 1);
+                for (int c = 0; c < nch && !stop; ++c) {
+                    const int kt1 = min(nkt, (c + 1) * CHUNK_TILES);
+                    for (int sa = s_lo; sa <= s_hi && !stop; ++sa)
+                        for (int kt = c * CHUNK_TILES; kt < kt1; ++kt, ++it) {
+                            const int st = it % STAGES;
+                            if (it >= STAGES && !mbar_wait(empty0 + 8 * st, ((it / STAGES) & 1) ^ 1)) {
+                                report_error(a.status, ELSI_ERR_TIMEOUT, 11);
+                                atomicExch(&aborted, 1);
+                                stop = true;
+                                break;
+                            }
+                            if (*(volatile int *)&aborted) { stop = true; break; }
+                            unsigned char *dst = smem + st * STAGE_BYTES;
+                            const unsigned full = full0 + 8 * st;
+                            mbar_expect_tx(full, STAGE_BYTES);
+                            tma_load_2d(smem_u32(dst), &maps.a, full, kt * BK, (sa - 1) * a.mpad + m0);
+                            tma_load_2d(smem_u32(dst + TILE_BYTES), &maps.b, full, kt * BK,
+                                        (L - sa - 1) * a.npad + n0);
+                            armed = it + 1;
+                        }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const unsigned idesc = idesc_f32acc(1, BM, BN);
+            int it = 0, g = 0;
+            bool stop = false;
+            for (int L = kOzD + 1; L >= 2 && !stop; --L) {
+                const int s_lo = max(1, L - kOzD), s_hi = min(kOzD, L - 1);
+                for (int c = 0; c < nch && !stop; ++c, ++g) {
+                    const int bsel = g & 1;
+                    if (g >= 2 && !mbar_wait(acce0 + 8 * bsel, ((g >> 1) - 1) & 1)) {
+                        report_error(a.status, ELSI_ERR_TIMEOUT, 12);
+                        atomicExch(&aborted, 1);
+                        stop = true;
+                        break;
+                    }
+                    const unsigned d = tmem + bsel * BN;
+                    const int kt1 = min(nkt, (c + 1) * CHUNK_TILES);
+                    bool first = true;
+                    for (int sa = s_lo; sa <= s_hi && !stop; ++sa)
+                        for (int kt = c * CHUNK_TILES; kt < kt1; ++kt, ++it) {
+                            const int st = it % STAGES;
+                            if (!mbar_wait(full0 + 8 * st, (it / STAGES) & 1)) {
+                                report_error(a.status, ELSI_ERR_TIMEOUT, 13);
+                                atomicExch(&aborted, 1);
+                                stop = true;
+                                break;
+                            }
+                            tc_fence_after();
+                            const unsigned base = smem_u32(smem + st * STAGE_BYTES);
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; ++kk) {
+                                const unsigned off = kk * 32;  // 16 bf16 along K
+                                mma_bf16(d, sdesc(base + off), sdesc(base + TILE_BYTES + off), idesc,
+                                         first ? 0u : 1u);
+                                first = false;
+                            }
+                            mma_commit(empty0 + 8 * st);
+                        }
+                    if (!stop) mma_commit(accf0 + 8 * bsel);
+                }
+            }
+        }
+    } else {
+        const int quarter = warp & 3;
+        const int row = m0 + quarter * 32 + lane;
+        const int er = (row < a.m_real) ? a.ea[row] : 0;
+        int iacc[BN];
+        bool ok = true;
+        int g = 0;
+        for (int L = kOzD + 1; L >= 2 && ok; --L) {
+#pragma unroll
+            for (int j = 0; j < BN; ++j) iacc[j] = 0;
+            for (int c = 0; c < nch; ++c, ++g) {
+                const int bsel = g & 1;
+                ok = mbar_wait(accf0 + 8 * bsel, (g >> 1) & 1);
+                if (!ok) {
+                    if (lane == 0) {
+                        report_error(a.status, ELSI_ERR_TIMEOUT, 14);
+                        atomicExch(&aborted, 1);
+                    }
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int q = 0; q < BN / 32; ++q) {
+                    float v[32];
+                    tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + bsel * BN + q * 32, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) iacc[q * 32 + j] += __float2int_rn(v[j]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce0 + 8 * bsel);
+            }
+            if (!ok || row >= a.m_real) continue;
+            // C (+)= alpha 2^(e_i + f_j - 7L) level sum, 16 columns at a time
+            const bool firstL = (L == kOzD + 1);
+            double *crow = a.C + (size_t)row;
+#pragma unroll
+            for (int q = 0; q < BN / 16; ++q) {
+                double cv[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + q * 16 + j;
+                    const bool in = col < a.n_real && (!a.uplo || row >= col);
+                    cv[j] = (in && (!firstL || a.beta != 0.0)) ? crow[(size_t)col * a.ldc] : 0.0;
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + q * 16 + j;
+                    if (col < a.n_real && (!a.uplo || row >= col)) {
+                        const double val =
+                            a.alpha * ldexp((double)iacc[q * 16 + j], er + a.eb[col] - kOzBits * L);
+                        crow[(size_t)col * a.ldc] = firstL ? fma(a.beta, cv[j], val) : cv[j] + val;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (aborted && warp == 0 && lane == 0) {
+        for (int it = (armed > STAGES ? armed - STAGES : 0); it < armed; ++it)
+            mbar_wait(full0 + 8 * (it % STAGES), (it / STAGES) & 1);
+    }
+    __syncthreads();
+    if (warp == 2) tmem_free(tmem, TMEM_COLS);
 }
 
 size_t ozaki_plane_elems(int V, int K)
@@ -275,25 +311,37 @@ cudaError_t ozaki_gemm(cudaStream_t st, int m, int n, int k, double alpha,
                        const __nv_bfloat16 *Ad, const int *ea, const __nv_bfloat16 *Bd,
                        const int *eb, double beta, double *C, int ldc, int uplo)
 {
+    using namespace oztc;
     if (m <= 0 || n <= 0) return cudaSuccess;
-    OzArgs a;
-    a.M = ceil_div(m, kOzBM) * kOzBM;
-    a.N = ceil_div(n, kOzBN) * kOzBN;
-    a.Kpad = ceil_div(k, kOzBK) * kOzBK;
-    a.A = Ad; a.a_plane = ozaki_plane_elems(m, k); a.ea = ea;
-    a.B = Bd; a.b_plane = ozaki_plane_elems(n, k); a.eb = eb;
-    a.alpha = alpha; a.beta = beta; a.C = C; a.ldc = ldc; a.m_real = m; a.n_real = n; a.uplo = uplo;
-    const size_t smem = (size_t)kOzStages * 2 * kOzD * kOzBM * kOzBK * 2;  // 172032
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    dim3 grid(a.M / kOzBM, a.N / kOzBN);
+    const int mpad = ceil_div(m, kOzBM) * kOzBM, npad = ceil_div(n, kOzBN) * kOzBN;
+    const int kpad = ceil_div(k, kOzBK) * kOzBK;
+    Maps maps;
+    if (!tc5::make_map_2d(&maps.a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Ad, (long long)kOzD * mpad, kpad,
+                          kpad, BK, BM) ||
+        !tc5::make_map_2d(&maps.b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Bd, (long long)kOzD * npad, kpad,
+                          kpad, BK, BN))
+        return cudaErrorNotSupported;
+    Args a;
+    a.m_real = m; a.n_real = n; a.kpad = kpad; a.mpad = mpad; a.npad = npad; a.uplo = uplo;
+    a.ldc = ldc; a.ea = ea; a.eb = eb; a.alpha = alpha; a.beta = beta; a.C = C;
+    float *tw;
+    size_t te;
+    int *ts = nullptr;
+    tc_scratch(&tw, &te, &ts);
+    static int *dummy_status = nullptr;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(ozaki_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        SMEM_BYTES);
+        if (attr_err == cudaSuccess) attr_err = cudaMalloc((void **)&dummy_status, 8 * sizeof(int));
+        if (attr_err == cudaSuccess) attr_err = cudaMemset(dummy_status, 0, 8 * sizeof(int));
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    a.status = ts ? ts : dummy_status;
+    dim3 grid(mpad / BM, npad / BN);
     EGB_COUNT_LAUNCH();
-    ozaki_gemm_kernel<<<grid, 256, smem, st>>>(a);
+    ozaki_gemm_tc_kernel<<<grid, 192, SMEM_BYTES, st>>>(maps, a);
     return cudaGetLastError();
 }
 

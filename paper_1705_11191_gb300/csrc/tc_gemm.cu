@@ -24,9 +24,12 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tcgen05.cuh"
 
 namespace egb {
 namespace tcg {
+
+using namespace tc5;
 
 constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3;
 constexpr int CH = 2;  // k-tiles per tensor-memory accumulation chunk (K = 64)
@@ -34,78 +37,6 @@ constexpr int TILE_BYTES = BM * BK * 4;  // 16 KB (BN == BM)
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int TMEM_COLS = 4 * BN;  // two buffers x (hi*hi sum, cross-term sum)
-constexpr long long kWaitLimit = 1ll << 22;
-
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on the phase with the given parity; false on expiry.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
-{
-    for (long long i = 0; i < kWaitLimit; ++i) {
-        if (mbar_try(bar, parity)) return true;
-        if (i > 32) __nanosleep(64);
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, unsigned bar,
-                                            int x, int y)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-        "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of 128 bytes,
-// 8-row groups 1024 bytes apart (SBO); LBO unused for this layout.
-__device__ __forceinline__ unsigned long long sdesc(unsigned saddr)
-{
-    unsigned long long d = 0;
-    d |= (unsigned long long)((saddr >> 4) & 0x3FFFu);
-    d |= (unsigned long long)1 << 16;
-    d |= (unsigned long long)(1024 >> 4) << 32;
-    d |= (unsigned long long)1 << 46;  // descriptor version of sm_100 family
-    d |= (unsigned long long)2 << 61;  // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: kind::tf32, FP32 accumulator, A and B K-major, M = 128, N = BN.
-__host__ __device__ constexpr unsigned idesc_tf32()
-{
-    return (1u << 4)                  // D format F32
-           | (2u << 7)                // A format TF32
-           | (2u << 10)               // B format TF32
-           | ((unsigned)(BN >> 3) << 17)
-           | ((unsigned)(BM >> 4) << 24);
-}
 
 __device__ __forceinline__ void mma_tf32(unsigned tmem_d, unsigned long long a, unsigned long long b,
                                          unsigned idesc, unsigned accum)
@@ -117,41 +48,10 @@ __device__ __forceinline__ void mma_tf32(unsigned tmem_d, unsigned long long a, 
         : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(unsigned bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 consecutive accumulator columns of this thread's lane (row).
-__device__ __forceinline__ void tmem_ld32(unsigned taddr, float *v)
-{
-    unsigned r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-
 struct Maps {
     CUtensorMap a_hi, a_lo, b_hi, b_lo;
 };
 
-__device__ __forceinline__ void mbar_arrive(unsigned bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 // Warps: 0 = TMA producer (one lane), 1 = MMA issuer (one lane), 2..5 = epilogue (warp w
 // reads tensor-memory lanes 32 (w mod 4) .. + 31, i.e. those rows of the tile). K is
@@ -222,7 +122,7 @@ gemm_tf32x3_kernel(const __grid_constant__ Maps maps, int m, int n, int kp, floa
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const unsigned idesc = idesc_tf32();
+            const unsigned idesc = idesc_f32acc(2, BM, BN);
             for (int kt = 0; kt < nk; ++kt) {
                 const int s = kt % STAGES, g = kt / CH, bsel = g & 1;
                 const unsigned ph = (kt / STAGES) & 1;
@@ -362,38 +262,10 @@ __global__ void split_planes_kernel(int rows, int k, int kw, int kp, int q_off,
     }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn()
-{
-    static EncodeTiledFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    });
-    return fn;
-}
-
 // rows x kp fp32 plane, K-major, boxes of 32 (K) x 128 (rows), 128-byte swizzle.
 static bool make_map(CUtensorMap *map, const float *plane, int rows, int kp)
 {
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)kp * sizeof(float)};
-    cuuint32_t box[2] = {BK, BM};
-    cuuint32_t estr[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)plane, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return make_map_2d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, plane, rows, kp, kp, BK, BM);
 }
 
 }  // namespace tcg
