@@ -98,27 +98,52 @@ static cudaError_t launch_potrf_diag(cudaStream_t st, int jb, T *a, int lda, T *
     return cudaGetLastError();
 }
 
+// Left-looking over panels of kTriPanel columns: the panel's diagonal block is factored by
+// kTriBlock blocks (updates inside the block), the rows below it are solved against the
+// panel's L (right triangular solve by blocks), and the trailing matrix gets one rank-
+// kTriPanel update per panel.
 template <typename T>
 cudaError_t potrf(cudaStream_t st, int n, T *a, int lda, T *inv_diag, T *work, int *status)
 {
-    const int nb = kTriBlock;
+    const int nb = kTriBlock, np = kTriPanel;
     cudaError_t e;
-    for (int j0 = 0; j0 < n; j0 += nb) {
-        int jb = (n - j0 < nb) ? n - j0 : nb;
-        T *a11 = a + j0 + (size_t)j0 * lda;
-        T *inv11 = inv_diag + j0;  // ld = n
-        if ((e = launch_potrf_diag<T>(st, jb, a11, lda, inv11, n, status, j0)) != cudaSuccess) return e;
-        int m2 = n - j0 - jb;
-        if (m2 > 0) {
-            T *a21 = a + (j0 + jb) + (size_t)j0 * lda;
-            T *a22 = a + (j0 + jb) + (size_t)(j0 + jb) * lda;
-            // L21 = A21 * inv(L11)^T
-            if ((e = gemm<T>(st, 0, 1, m2, jb, jb, T(1), a21, lda, inv11, n, T(0), work, m2)) != cudaSuccess) return e;
-            if ((e = cudaMemcpy2DAsync(a21, sizeof(T) * lda, work, sizeof(T) * m2, sizeof(T) * m2, jb,
-                                       cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
-            // A22 -= L21 L21^T (lower triangle)
-            if ((e = gemm<T>(st, 0, 1, m2, m2, jb, T(-1), a21, lda, a21, lda, T(1), a22, lda, 1)) != cudaSuccess) return e;
+    for (int p0 = 0; p0 < n; p0 += np) {
+        const int p1 = (n - p0 < np) ? n : p0 + np;
+        // (1) diagonal block [p0, p1)
+        for (int j0 = p0; j0 < p1; j0 += nb) {
+            const int jb = (p1 - j0 < nb) ? p1 - j0 : nb;
+            T *a11 = a + j0 + (size_t)j0 * lda;
+            T *inv11 = inv_diag + j0;  // ld = n
+            if ((e = launch_potrf_diag<T>(st, jb, a11, lda, inv11, n, status, j0)) != cudaSuccess) return e;
+            const int m2 = p1 - j0 - jb;
+            if (m2 > 0) {
+                T *a21 = a + (j0 + jb) + (size_t)j0 * lda;
+                T *a22 = a + (j0 + jb) + (size_t)(j0 + jb) * lda;
+                if ((e = gemm<T>(st, 0, 1, m2, jb, jb, T(1), a21, lda, inv11, n, T(0), work, m2)) != cudaSuccess) return e;
+                if ((e = cudaMemcpy2DAsync(a21, sizeof(T) * lda, work, sizeof(T) * m2, sizeof(T) * m2, jb,
+                                           cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+                if ((e = gemm<T>(st, 0, 1, m2, m2, jb, T(-1), a21, lda, a21, lda, T(1), a22, lda, 1)) != cudaSuccess) return e;
+            }
         }
+        const int m2 = n - p1;
+        if (m2 <= 0) continue;
+        // (2) rows below: X L_pp^T = A21, block column by block column
+        T *a21 = a + p1 + (size_t)p0 * lda;
+        for (int j0 = p0; j0 < p1; j0 += nb) {
+            const int jb = (p1 - j0 < nb) ? p1 - j0 : nb;
+            T *xj = a + p1 + (size_t)j0 * lda;
+            if (j0 > p0) {
+                // A21_j -= X_{p0..j0} L_{j, p0..j0}^T
+                if ((e = gemm<T>(st, 0, 1, m2, jb, j0 - p0, T(-1), a21, lda, a + j0 + (size_t)p0 * lda, lda,
+                                 T(1), xj, lda)) != cudaSuccess) return e;
+            }
+            if ((e = gemm<T>(st, 0, 1, m2, jb, jb, T(1), xj, lda, inv_diag + j0, n, T(0), work, m2)) != cudaSuccess) return e;
+            if ((e = cudaMemcpy2DAsync(xj, sizeof(T) * lda, work, sizeof(T) * m2, sizeof(T) * m2, jb,
+                                       cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+        }
+        // (3) A22 -= L21 L21^T (lower triangle), K = panel width
+        T *a22 = a + p1 + (size_t)p1 * lda;
+        if ((e = gemm<T>(st, 0, 1, m2, m2, p1 - p0, T(-1), a21, lda, a21, lda, T(1), a22, lda, 1)) != cudaSuccess) return e;
     }
     size_t total = (size_t)n * n;
     int grid = (int)((total + 255) / 256);
@@ -128,34 +153,64 @@ cudaError_t potrf(cudaStream_t st, int n, T *a, int lda, T *inv_diag, T *work, i
     return cudaGetLastError();
 }
 
+// Triangular solve restricted to the row range [r0, r1): the blocks of kTriBlock rows in the
+// range are solved one after another and each updates only the rows of the range.
 template <typename T>
-cudaError_t trsm_left_lower(cudaStream_t st, int trans, int n, int ncol, const T *L, int ldl,
-                            const T *inv_diag, T *B, int ldb, T *work)
+static cudaError_t trsm_range(cudaStream_t st, int trans, int r0, int r1, int ncol, const T *L,
+                              int ldl, const T *inv_diag, int ldi, T *B, int ldb, T *work)
 {
     const int nb = kTriBlock;
     cudaError_t e;
-    if (n <= 0 || ncol <= 0) return cudaSuccess;
-    const int nblk = ceil_div(n, nb);
+    const int nblk = ceil_div(r1 - r0, nb);
     for (int bi = 0; bi < nblk; ++bi) {
-        int blk = trans ? (nblk - 1 - bi) : bi;
-        int j0 = blk * nb;
-        int jb = (n - j0 < nb) ? n - j0 : nb;
-        const T *inv11 = inv_diag + j0;  // ld n
+        const int blk = trans ? (nblk - 1 - bi) : bi;
+        const int j0 = r0 + blk * nb;
+        const int jb = (r1 - j0 < nb) ? r1 - j0 : nb;
+        const T *inv11 = inv_diag + j0;
         T *bj = B + j0;
         // B_j := inv(L_jj) B_j   or   inv(L_jj)^T B_j
-        if ((e = gemm<T>(st, trans, 0, jb, ncol, jb, T(1), inv11, n, bj, ldb, T(0), work, jb)) != cudaSuccess) return e;
+        if ((e = gemm<T>(st, trans, 0, jb, ncol, jb, T(1), inv11, ldi, bj, ldb, T(0), work, jb)) != cudaSuccess) return e;
         if ((e = cudaMemcpy2DAsync(bj, sizeof(T) * ldb, work, sizeof(T) * jb, sizeof(T) * jb, ncol,
                                    cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
         if (!trans) {
-            int m2 = n - j0 - jb;
+            const int m2 = r1 - j0 - jb;
             if (m2 > 0) {
                 const T *l21 = L + (j0 + jb) + (size_t)j0 * ldl;
                 if ((e = gemm<T>(st, 0, 0, m2, ncol, jb, T(-1), l21, ldl, bj, ldb, T(1), B + j0 + jb, ldb)) != cudaSuccess) return e;
             }
-        } else if (j0 > 0) {
-            // B_{<j} -= (L_{j,<j})^T B_j ; L_{j,<j} is jb x j0 at rows j0
-            const T *lj = L + j0;
-            if ((e = gemm<T>(st, 1, 0, j0, ncol, jb, T(-1), lj, ldl, bj, ldb, T(1), B, ldb)) != cudaSuccess) return e;
+        } else if (j0 > r0) {
+            // B_{r0..j0} -= (L_{j, r0..j0})^T B_j
+            const T *lj = L + j0 + (size_t)r0 * ldl;
+            if ((e = gemm<T>(st, 1, 0, j0 - r0, ncol, jb, T(-1), lj, ldl, bj, ldb, T(1), B + r0, ldb)) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+// Two block levels: panels of kTriPanel rows are solved by trsm_range (kTriBlock blocks with
+// updates inside the panel); the rest of B is updated once per panel with K = kTriPanel,
+// which keeps the read-modify-write traffic on B at n / kTriPanel passes.
+template <typename T>
+cudaError_t trsm_left_lower(cudaStream_t st, int trans, int n, int ncol, const T *L, int ldl,
+                            const T *inv_diag, T *B, int ldb, T *work)
+{
+    constexpr int np = kTriPanel;
+    cudaError_t e;
+    if (n <= 0 || ncol <= 0) return cudaSuccess;
+    const int npan = ceil_div(n, np);
+    for (int pi = 0; pi < npan; ++pi) {
+        const int pan = trans ? (npan - 1 - pi) : pi;
+        const int r0 = pan * np, r1 = (n - r0 < np) ? n : r0 + np;
+        if ((e = trsm_range<T>(st, trans, r0, r1, ncol, L, ldl, inv_diag, n, B, ldb, work)) != cudaSuccess) return e;
+        if (!trans) {
+            if (r1 < n) {
+                // B_{r1..n} -= L_{r1..n, r0..r1} B_{r0..r1}
+                if ((e = gemm<T>(st, 0, 0, n - r1, ncol, r1 - r0, T(-1), L + r1 + (size_t)r0 * ldl, ldl,
+                                 B + r0, ldb, T(1), B + r1, ldb)) != cudaSuccess) return e;
+            }
+        } else if (r0 > 0) {
+            // B_{0..r0} -= (L_{r0..r1, 0..r0})^T B_{r0..r1}
+            if ((e = gemm<T>(st, 1, 0, r0, ncol, r1 - r0, T(-1), L + r0, ldl, B + r0, ldb, T(1), B, ldb)) != cudaSuccess) return e;
         }
     }
     return cudaSuccess;

@@ -72,7 +72,8 @@ cudaError_t check_finite(cudaStream_t st, int m, int n, const T *a, int lda, int
 // j*nb). work: n x nb scratch. Status ELSI_ERR_NOT_PD with the pivot on failure.
 template <typename T>
 cudaError_t potrf(cudaStream_t st, int n, T *a, int lda, T *inv_diag, T *work, int *status);
-constexpr int kTriBlock = 64;  // nb of potrf / trsm
+constexpr int kTriBlock = 64;   // nb of potrf / trsm
+constexpr int kTriPanel = 256;  // outer panel of trsm (rank-256 updates of the rest of B)
 
 // B (n x ncol) := L^{-1} B (trans = 0) or L^{-T} B (trans = 1), L lower from potrf,
 // inv_diag its diagonal-block inverses. work: kTriBlock x ncol scratch.

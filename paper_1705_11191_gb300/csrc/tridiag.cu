@@ -312,9 +312,12 @@ __device__ __forceinline__ double hash_unit(unsigned a, unsigned b)
 // closer than tol_rel * ||T||. A vector that the projection nearly annihilates (its
 // eigenvalue coincides with an earlier one to working accuracy, as for the pairs of the
 // real form of a complex Hermitian matrix) is replaced by one step of inverse iteration
-// on its block, x = (T_b - lambda I)^{-1} b for a pseudo-random b, using the L+ D+ L+^T
-// factors that the twisted factorisation left in dplus (the vector's spent U- column
-// holds the intermediate values), and is then projected and normalised again.
+// on its block, x = (T_b - lambda I)^{-1} b for a pseudo-random b orthogonal to the
+// cluster's vectors, using the L+ D+ L+^T factors that the twisted factorisation left in
+// dplus (the vector's spent U- column holds the intermediate values), and is then
+// projected and normalised again. When lambda sits much closer to an accepted vector's
+// eigenvalue than to its own, that vector dominates x; what is left after the projection
+// is still accurate as long as it is far above the rounding level.
 template <typename T>
 __global__ void cluster_orth_kernel(int n, int kvec, const double *w, const double *e,
                                     const double *bounds, const int *blk, double tol_rel,
@@ -330,16 +333,26 @@ __global__ void cluster_orth_kernel(int n, int kvec, const double *w, const doub
     for (int v = i0 + 1; v < i1; ++v) {
         T *zv = z + (size_t)v * ldz;
         double s = cluster_project(n, i0, v, z, ldz, red);
-        for (int attempt = 0; attempt < 3 && s < 1e-4; ++attempt) {
+        // a regenerated vector is accepted when its part orthogonal to the cluster is far
+        // above the rounding level of T (its direction error is then eps / sqrt(s))
+        const double accept = sizeof(T) == 8 ? 1e-16 : 1e-8;
+        bool regen = false;
+        for (int attempt = 0; attempt < 3 && s < (regen ? accept : 1e-4); ++attempt) {
+            regen = true;
+            const int bs = blk[2 * v], be = blk[2 * v + 1];
+            // start b: pseudo-random on the block, orthogonal to the cluster's vectors
+            for (int i = threadIdx.x; i < n; i += blockDim.x)
+                zv[i] = (i >= bs && i < be) ? (T)hash_unit((unsigned)(v * 7919 + attempt), (unsigned)i) : T(0);
+            __syncthreads();
+            cluster_project(n, i0, v, z, ldz, red);
             if (threadIdx.x == 0) {
-                const int bs = blk[2 * v], be = blk[2 * v + 1];
                 double *x = work + v;  // x[i * kvec]
                 // forward: L+ y = b; backward: L+^T x = D+^{-1} y. Entries are rescaled
                 // (all at once) whenever one exceeds 2^500.
                 const double big = 0x1p500, shrink = 0x1p-500;
                 double y = 0.0;
                 for (int i = bs; i < be; ++i) {
-                    const double bi = hash_unit((unsigned)(v * 7919 + attempt), (unsigned)i);
+                    const double bi = (double)zv[i];
                     y = (i == bs) ? bi : bi - (e[i - 1] / dplus[(size_t)(i - 1) * kvec + v]) * y;
                     if (fabs(y) > big) {
                         for (int j = bs; j < i; ++j) x[(size_t)j * kvec] *= shrink;
@@ -373,7 +386,7 @@ __global__ void cluster_orth_kernel(int n, int kvec, const double *w, const doub
             __syncthreads();
             s = cluster_project(n, i0, v, z, ldz, red);
         }
-        if (s < 1e-4) {
+        if (s < (regen ? accept : 1e-4)) {
             if (threadIdx.x == 0) report_error(status, ELSI_ERR_NO_CONVERGENCE, v);
             return;
         }
