@@ -242,7 +242,8 @@ def main():
 
     # roofline of the dominant stage
     dom = max(stages, key=stages.get)
-    out["roofline"] = roofline_for(dom, stages[dom], n, k, prec, out["clocks"])
+    out["roofline"] = roofline_for(dom, stages[dom], n, k, prec, out["clocks"],
+                                   refine_iters=max(iters, 0))
 
     # binary64 arm and the relative error of P between the two routes
     if not args.no_fp64 and rank == 0 and prec == egb.PREC_FP32_REFINE:
@@ -296,34 +297,76 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def roofline_for(stage: str, stage_ms: float, n: int, k: int, prec: int, clocks: dict):
-    """Roofline entry for the dominant stage (algorithmic flops per launch of the stage /
-    its measured device time)."""
-    import math
-    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    fp64_peak = FP64_FLOP_PER_CLK * 2070e6 / 1e12  # TFLOP/s at the maximum SM clock
+# dominant kernel of each stage of the binary32+refinement route (one launch per solve
+# unless noted) and its roofline class
+_STAGE_KERNEL = {
+    "back_q2": ("q2_apply_tc_kernel", "tensor", "tf32"),
+    "band_to_tri": ("chase_kernel<float>", "hbm", None),
+    "refine": ("ozaki_gemm_tc_kernel (all launches of the stage)", "tensor", "bf16"),
+    "full_to_band": ("gemm_tf32x3_kernel + panel_qr_kernel<float>", "tensor", "tf32"),
+    "back_q1": ("gemm_tf32x3_kernel", "tensor", "tf32"),
+    "standard_form": ("gemm_tf32x3_kernel", "tensor", "tf32"),
+    "tridiag_solve": ("bisect_kernel<2>", "alu", None),
+}
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tf32 / bf16 tensor rates
+
+
+def roofline_for(stage: str, stage_ms: float, n: int, k: int, prec: int, clocks: dict,
+                 refine_iters: int = 4, band: int = 64):
+    """Roofline entry for the dominant stage: algorithmic work of its launch(es) per solve
+    divided by the stage's device time (CUDA events recorded on the solve stream around
+    the stage). Tensor-core stages take the measured sustained bf16 rate (times the nominal
+    tf32/bf16 ratio for tf32 work); the bulge chase is reported as band traffic against the
+    measured copy bandwidth."""
+    peaks = {}
+    try:
+        with open(PEAKS_FILE) as fh:
+            peaks = json.load(fh)
+        src = "of measured"
+    except OSError:
+        src = "of fallback"
+    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    kern, bound, dt = _STAGE_KERNEL.get(stage, (stage, "latency", None))
+    nv = n if prec == 1 else k  # vectors carried through the back-transformations
+    out = {"stage": stage, "kernel": kern, "traffic": None}
+    sec = stage_ms * 1e-3
+    if prec == 1 and stage == "band_to_tri":
+        # per (sweep, step) task: read and write the b x b block X and the b x b block D
+        tasks = sum((n - 2 - j) // band + 1 for j in range(n - 2))
+        bytes_ = tasks * 4.0 * band * band * 4
+        ach = bytes_ / sec / 1e9
+        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                   peak_note=f"hbm_gbs {src} (copy bandwidth); band bytes = tasks x 4 b^2 x 4 B")
+        return out
     flops = {
         "cholesky": n ** 3 / 3.0,
         "standard_form": 2.0 * n ** 3,
         "full_to_band": 4.0 * n ** 3 / 3.0,
-        "back_q1": 2.0 * n * n * (n if prec == 1 else k),
-        "back_q2": 2.0 * n * n * (n if prec == 1 else k),
-        "back_subst": 1.0 * n * n * (n if prec == 1 else k),
+        "back_q1": 2.0 * n * n * nv,
+        "back_q2": 2.0 * n * n * nv,
+        "back_subst": 1.0 * n * n * nv,
         "density": 2.0 * n * n * k,
-        "refine": 4.0 * n * n * k * 4 + 4.0 * n * k * k * 4,
+        # digit products of the binary64-accurate products: 28 bf16 GEMMs per product;
+        # per pass H X, S X (n x k x n) and X^T Y_H, X^T Y_S (k x k x n)
+        "refine": 28 * 2.0 * (2.0 * n * n * k + 2.0 * k * k * n) * (refine_iters + 1),
     }.get(stage)
-    if flops is None:
-        return {"bound": "latency", "stage": stage, "achieved": None, "peak": None,
-                "unit": None, "frac": None, "traffic": None}
-    achieved = flops / (stage_ms * 1e-3) / 1e12
-    if prec == 0 or stage == "refine":
-        return {"bound": "alu", "stage": stage, "achieved": achieved, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
-                "peak_note": "binary64 FMA rate derived from 152 SMs x 2 DFMA/clk x 2070 MHz"}
-    fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12
-    return {"bound": "alu", "stage": stage, "achieved": achieved, "peak": fp32_peak,
-            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-            "peak_note": "binary32 FMA rate derived from 152 SMs x 128 FFMA/clk x 2070 MHz"}
+    if flops is None or prec == 0:
+        fp64_peak = FP64_FLOP_PER_CLK * 2070e6 / 1e12
+        f = flops if flops is not None else 0.0
+        ach = f / sec / 1e12 if flops else None
+        out.update(bound="alu", achieved=ach, peak=fp64_peak, unit="TFLOP/s",
+                   frac=(ach / fp64_peak) if ach else None,
+                   peak_note="binary64 FMA rate derived from 152 SMs x 2 DFMA/clk x 2070 MHz")
+        return out
+    peak = bf16 * (TF32_PER_BF16 if dt == "tf32" else 1.0)
+    ach = flops / sec / 1e12
+    out.update(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+               peak_note=(f"bf16_tflops_sustained {src}" +
+                          (" x nominal tf32/bf16 ratio 1.1/2.25" if dt == "tf32" else "") +
+                          ("; tf32 work counted once (the three split products are not counted)"
+                           if dt == "tf32" else "; 28 digit products per binary64-accurate product")))
+    return out
 
 
 if __name__ == "__main__":

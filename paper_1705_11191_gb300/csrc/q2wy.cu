@@ -8,7 +8,7 @@
 // columns (column a = sweep J+m-1-a, shifted down by J+m-1-a-J rows) and T is the upper
 // triangular factor of the forward accumulation (Schreiber & Van Loan's compact WY).
 // T is computed once per group (q2_tfactor_kernel); the application kernel keeps the
-// current window of its 64 columns of Z in a shared-memory ring and performs, per group,
+// current window of its 128 columns of Z in a shared-memory ring and performs, per group,
 //     Y = V^T Z_w,  Y = T^T Y,  Z_w -= V Y
 // with mma.sync m16n8k8 TF32 products in three-pass split precision
 // (x = x_hi + x_lo, x_hi = tf32(x); A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi), which keeps
@@ -20,14 +20,14 @@ namespace egb {
 
 constexpr int kWyM = 64;          // reflectors per group (sweeps per block)
 constexpr int kWyRows = 128;      // window rows covered (m + b - 1 <= 127)
-constexpr int kWyCols = 64;       // columns of Z per CTA
+constexpr int kWyCols = 128;      // columns of Z per CTA (8 warps x 16)
 constexpr int kWyRing = 256;      // ring rows (power of two)
 constexpr int kWyRingLd = kWyRing + 4;
 constexpr int kWyVtLd = kWyRows + 8;   // V^T rows (a) stride
 constexpr int kWyTLd = kWyM + 4;
 constexpr int kWyYLd = kWyM + 4;
 
-constexpr int kWyGroupWords = 2 * kWyM * kWyRows + 2 * kWyM * kWyM;
+constexpr int kWyGroupWords = kWyM * kWyRows + kWyM * kWyM;
 
 __device__ __forceinline__ int wy_steps(int n, int b, int j) { return (n - 2 - j) / b + 1; }
 
@@ -46,9 +46,8 @@ __device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo)
 
 // ---------------------------------------------------------------- T factors
 // One CTA (128 threads) per group g = jb * S + t. Writes, for the application kernel,
-// the group's V^T (64 x 128, [a][window row]) and T^T (64 x 64, [a][c] = T[c][a]), each as
-// two TF32 planes (hi = tf32(x), lo = tf32(x - hi)); layout per group:
-// [Vt hi | Vt lo | Tt hi | Tt lo] = kWyGroupWords words. Reflectors with tau = 0 (none or
+// the group's V^T (64 x 128, [a][window row]) and T^T (64 x 64, [a][c] = T[c][a]) in
+// binary32; layout per group: [Vt | Tt] = kWyGroupWords words. Reflectors with tau = 0 (none or
 // trivial) are treated as zero columns of V, which does not change I - V T V^T.
 // T is built by blocks: the 8 diagonal 8 x 8 blocks by the forward recurrence, then
 // pairs of blocks are merged, T = [[T1, -T1 (V1^T V2) T2], [0, T2]], for block sizes
@@ -139,44 +138,15 @@ __global__ void __launch_bounds__(128) q2_tfactor_kernel(int n, int b, int S, in
     for (int e = tid; e < kWyM * kWyRows; e += blockDim.x) {
         int a = e / kWyRows, r = e % kWyRows;
         int i = r - (Jend - 1 - a - J);
-        float v = (i >= 0 && i < 64) ? Vc[a][i] : 0.f;
-        unsigned hi, lo;
-        split_tf32(v, hi, lo);
-        gw[e] = hi;
-        gw[kWyM * kWyRows + e] = lo;
+        gw[e] = __float_as_uint((i >= 0 && i < 64) ? Vc[a][i] : 0.f);
     }
     for (int e = tid; e < kWyM * kWyM; e += blockDim.x) {
         int a = e / kWyM, c = e % kWyM;
-        unsigned hi, lo;
-        split_tf32(Tm[c][a], hi, lo);  // T^T row-major
-        gw[2 * kWyM * kWyRows + e] = hi;
-        gw[2 * kWyM * kWyRows + kWyM * kWyM + e] = lo;
+        gw[kWyM * kWyRows + e] = __float_as_uint(Tm[c][a]);  // T^T row-major
     }
 }
 
 // ---------------------------------------------------------------- application
-__device__ __forceinline__ void mma_tf32(float *c, const unsigned *a, unsigned b0, unsigned b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// three-pass split product accumulate: c += A B (A: 16x8 fragment values, B: 8x8)
-__device__ __forceinline__ void mma3(float *c, const float *av, float b0v, float b1v)
-{
-    unsigned ah[4], al[4], bh0, bl0, bh1, bl1;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) split_tf32(av[q], ah[q], al[q]);
-    split_tf32(b0v, bh0, bl0);
-    split_tf32(b1v, bh1, bl1);
-    mma_tf32(c, al, bh0, bh1);
-    mma_tf32(c, ah, bl0, bl1);
-    mma_tf32(c, ah, bh0, bh1);
-}
-
 __device__ __forceinline__ void wy_cp_async4(float *dst, const float *src)
 {
     unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -202,27 +172,35 @@ __device__ __forceinline__ void wy_cp_async16(void *dst, const void *src)
 constexpr int kWyVLd = kWyRows + 8;   // 136 words
 constexpr int kWyTLd2 = kWyM + 4;     // 68 words
 constexpr int kWyWcols = 16;          // columns per warp
+constexpr int kWyWarps = kWyCols / kWyWcols;
 
-// CTA: 128 threads (4 warps), 64 columns of Z; warp w owns columns [16w, 16w+16) in all
-// three products, so only the staging of V and T needs a block-wide barrier.
-__global__ void __launch_bounds__(128) q2_apply_tc_kernel(int n, int b, int S, const float *__restrict__ tfac,
+__device__ __forceinline__ void split4(const float *v, unsigned *h, unsigned *l)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) split_tf32(v[q], h[q], l[q]);
+}
+
+// CTA: 256 threads (8 warps), 128 columns of Z; warp w owns columns [16w, 16w+16) in all
+// three products, so only the staging of V and T needs a block-wide barrier. V^T and T^T are
+// staged in binary32 and split into TF32 hi / lo parts as the fragments are read. The
+// reflectors of a group form a band in the window (reflector a covers window rows
+// off_a .. off_a + b - 1, off_a = m - 1 - a for the group's m reflectors), so the products
+// with V skip the blocks of 16 x 8 that are zero.
+__global__ void __launch_bounds__(256) q2_apply_tc_kernel(int n, int b, int S, const float *__restrict__ tfac,
                                                           int k, float *z, int ldz)
 {
     extern __shared__ __align__(16) unsigned wsm[];
     float *ring = reinterpret_cast<float *>(wsm);                  // [col][slot]
-    unsigned *Vh = wsm + kWyCols * kWyRingLd;                      // [a][row]
-    unsigned *Vl = Vh + kWyM * kWyVLd;
-    unsigned *Th = Vl + kWyM * kWyVLd;                             // T^T [a][c]
-    unsigned *Tl = Th + kWyM * kWyTLd2;
-    unsigned *Yw = Tl + kWyM * kWyTLd2;                            // per warp: hi, lo [col][a]
+    float *Vs = ring + kWyCols * kWyRingLd;                        // V^T [a][row]
+    float *Ts = Vs + kWyM * kWyVLd;                                // T^T [a][c]
+    float *Yall = Ts + kWyM * kWyTLd2;                             // per warp: [col][a]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gq = lane >> 2, tq = lane & 3;
     const int c0 = blockIdx.x * kWyCols;
     const int wc0 = warp * kWyWcols;                               // first local column of the warp
     const int ncol = min(kWyCols, k - c0);
     const int wncol = max(0, min(kWyWcols, ncol - wc0));
-    unsigned *Yh = Yw + warp * 2 * kWyWcols * kWyTLd2;
-    unsigned *Yl = Yh + kWyWcols * kWyTLd2;
+    float *Y = Yall + warp * kWyWcols * kWyTLd2;
     const int nsweep = n - 2;
     const int nblk = (nsweep + kWyM - 1) / kWyM;
 
@@ -246,6 +224,7 @@ __global__ void __launch_bounds__(128) q2_apply_tc_kernel(int n, int b, int S, c
     for (int jb = nblk - 1; jb >= 0; --jb) {
         const int J = jb * kWyM;
         const int Jend = min(nsweep, J + kWyM);
+        const int mA = Jend - J;  // reflectors of this block (columns a >= mA of V are zero)
         const int SJ = wy_steps(n, b, J);
         int lo = J + 1;
         int hi = min(n, Jend + b);
@@ -255,20 +234,17 @@ __global__ void __launch_bounds__(128) q2_apply_tc_kernel(int n, int b, int S, c
         fetch_rows(lo, hi);
         asm volatile("cp.async.commit_group;\n" ::);
         for (int t = 0; t < SJ; ++t) {
-            // ---- stage V^T and T^T planes of group (jb, t) (everyone finished step t-1)
+            // ---- stage V^T and T^T of group (jb, t) (everyone finished step t-1)
             __syncthreads();
             {
-                const unsigned *gsrc = reinterpret_cast<const unsigned *>(tfac) + ((size_t)jb * S + t) * kWyGroupWords;
-                // V planes: 2 x 64 rows x 32 chunks; T planes: 2 x 64 rows x 16 chunks
-                for (int e = tid; e < 2 * kWyM * 32; e += 128) {
-                    int pl = e / (kWyM * 32), rem = e % (kWyM * 32), a = rem / 32, ch = rem % 32;
-                    unsigned *dst = (pl ? Vl : Vh) + a * kWyVLd + ch * 4;
-                    wy_cp_async16(dst, gsrc + pl * kWyM * kWyRows + a * kWyRows + ch * 4);
+                const float *gsrc = tfac + ((size_t)jb * S + t) * kWyGroupWords;
+                for (int e = tid; e < kWyM * 32; e += 256) {  // 64 rows x 32 chunks of 4
+                    int a = e >> 5, ch = e & 31;
+                    wy_cp_async16(Vs + a * kWyVLd + ch * 4, gsrc + a * kWyRows + ch * 4);
                 }
-                for (int e = tid; e < 2 * kWyM * 16; e += 128) {
-                    int pl = e / (kWyM * 16), rem = e % (kWyM * 16), a = rem / 16, ch = rem % 16;
-                    unsigned *dst = (pl ? Tl : Th) + a * kWyTLd2 + ch * 4;
-                    wy_cp_async16(dst, gsrc + 2 * kWyM * kWyRows + pl * kWyM * kWyM + a * kWyM + ch * 4);
+                for (int e = tid; e < kWyM * 16; e += 256) {  // 64 rows x 16 chunks
+                    int a = e >> 4, ch = e & 15;
+                    wy_cp_async16(Ts + a * kWyTLd2 + ch * 4, gsrc + kWyM * kWyRows + a * kWyM + ch * 4);
                 }
                 asm volatile("cp.async.commit_group;\n" ::);
             }
@@ -281,54 +257,52 @@ __global__ void __launch_bounds__(128) q2_apply_tc_kernel(int n, int b, int S, c
             const int wrows = hi - lo;
 
             // ---- Y (64 x 16) = V^T Z_w[:, own columns]
-            {
-                float acc[4][2][4];
+#pragma unroll 1
+            for (int im = 0; im < 4; ++im) {
+                const int am = im * 16;
+                float acc[2][4];
 #pragma unroll
-                for (int im = 0; im < 4; ++im)
+                for (int jn = 0; jn < 2; ++jn)
 #pragma unroll
-                    for (int jn = 0; jn < 2; ++jn)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[im][jn][q] = 0.f;
-                for (int k0 = 0; k0 < wrows; k0 += 8) {
-                    unsigned bh[2][2], bl[2][2];
-#pragma unroll
-                    for (int jn = 0; jn < 2; ++jn) {
-                        const int col = wc0 + jn * 8 + gq;
-                        float x0 = (k0 + tq < wrows) ? rs(col, lo + k0 + tq) : 0.f;
-                        float x1 = (k0 + tq + 4 < wrows) ? rs(col, lo + k0 + tq + 4) : 0.f;
-                        split_tf32(x0, bh[jn][0], bl[jn][0]);
-                        split_tf32(x1, bh[jn][1], bl[jn][1]);
-                    }
-#pragma unroll
-                    for (int im = 0; im < 4; ++im) {
-                        const int am = im * 16;
-                        const int i0 = (am + gq) * kWyVLd + k0 + tq, i1 = (am + gq + 8) * kWyVLd + k0 + tq;
-                        unsigned ah0 = Vh[i0], ah1 = Vh[i1], ah2 = Vh[i0 + 4], ah3 = Vh[i1 + 4];
-                        unsigned al0 = Vl[i0], al1 = Vl[i1], al2 = Vl[i0 + 4], al3 = Vl[i1 + 4];
+                    for (int q = 0; q < 4; ++q) acc[jn][q] = 0.f;
+                if (am < mA) {
+                    // window rows covered by reflectors am .. am + 15
+                    const int alast = min(am + 15, mA - 1);
+                    const int klo = ((mA - 1 - alast) / 8) * 8;
+                    const int khi = min(wrows, mA - 1 - am + b);
+                    for (int k0 = klo; k0 < khi; k0 += 8) {
+                        unsigned bh[2][2], bl[2][2];
 #pragma unroll
                         for (int jn = 0; jn < 2; ++jn) {
-                            mma_tf32_raw(acc[im][jn], al0, al1, al2, al3, bh[jn][0], bh[jn][1]);
-                            mma_tf32_raw(acc[im][jn], ah0, ah1, ah2, ah3, bl[jn][0], bl[jn][1]);
-                            mma_tf32_raw(acc[im][jn], ah0, ah1, ah2, ah3, bh[jn][0], bh[jn][1]);
+                            const int col = wc0 + jn * 8 + gq;
+                            float x0 = (k0 + tq < wrows) ? rs(col, lo + k0 + tq) : 0.f;
+                            float x1 = (k0 + tq + 4 < wrows) ? rs(col, lo + k0 + tq + 4) : 0.f;
+                            split_tf32(x0, bh[jn][0], bl[jn][0]);
+                            split_tf32(x1, bh[jn][1], bl[jn][1]);
+                        }
+                        const int i0 = (am + gq) * kWyVLd + k0 + tq, i1 = (am + gq + 8) * kWyVLd + k0 + tq;
+                        const float av[4] = {Vs[i0], Vs[i1], Vs[i0 + 4], Vs[i1 + 4]};
+                        unsigned ah[4], al[4];
+                        split4(av, ah, al);
+#pragma unroll
+                        for (int jn = 0; jn < 2; ++jn) {
+                            mma_tf32_raw(acc[jn], al[0], al[1], al[2], al[3], bh[jn][0], bh[jn][1]);
+                            mma_tf32_raw(acc[jn], ah[0], ah[1], ah[2], ah[3], bl[jn][0], bl[jn][1]);
+                            mma_tf32_raw(acc[jn], ah[0], ah[1], ah[2], ah[3], bh[jn][0], bh[jn][1]);
                         }
                     }
                 }
-                // Y -> warp scratch as split B operand of the next product: [col][a]
+                // Y -> warp scratch as the B operand of the next product: [col][a]
 #pragma unroll
-                for (int im = 0; im < 4; ++im)
+                for (int jn = 0; jn < 2; ++jn)
 #pragma unroll
-                    for (int jn = 0; jn < 2; ++jn)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int a = im * 16 + gq + (q >> 1) * 8, col = jn * 8 + 2 * tq + (q & 1);
-                            unsigned hv, lv;
-                            split_tf32(acc[im][jn][q], hv, lv);
-                            Yh[col * kWyTLd2 + a] = hv;
-                            Yl[col * kWyTLd2 + a] = lv;
-                        }
+                    for (int q = 0; q < 4; ++q) {
+                        const int a = am + gq + (q >> 1) * 8, col = jn * 8 + 2 * tq + (q & 1);
+                        Y[col * kWyTLd2 + a] = acc[jn][q];
+                    }
             }
             __syncwarp();
-            // ---- Y2 = T^T Y (64 x 16), stored negated and split
+            // ---- Y2 = T^T Y (64 x 16), stored negated
             {
                 float acc[4][2][4];
 #pragma unroll
@@ -343,22 +317,21 @@ __global__ void __launch_bounds__(128) q2_apply_tc_kernel(int n, int b, int S, c
 #pragma unroll
                     for (int jn = 0; jn < 2; ++jn) {
                         const int col = jn * 8 + gq;
-                        bh[jn][0] = Yh[col * kWyTLd2 + k0 + tq];
-                        bh[jn][1] = Yh[col * kWyTLd2 + k0 + tq + 4];
-                        bl[jn][0] = Yl[col * kWyTLd2 + k0 + tq];
-                        bl[jn][1] = Yl[col * kWyTLd2 + k0 + tq + 4];
+                        split_tf32(Y[col * kWyTLd2 + k0 + tq], bh[jn][0], bl[jn][0]);
+                        split_tf32(Y[col * kWyTLd2 + k0 + tq + 4], bh[jn][1], bl[jn][1]);
                     }
 #pragma unroll
                     for (int im = 0; im < 4; ++im) {
                         const int am = im * 16;
                         const int i0 = (am + gq) * kWyTLd2 + k0 + tq, i1 = (am + gq + 8) * kWyTLd2 + k0 + tq;
-                        unsigned ah0 = Th[i0], ah1 = Th[i1], ah2 = Th[i0 + 4], ah3 = Th[i1 + 4];
-                        unsigned al0 = Tl[i0], al1 = Tl[i1], al2 = Tl[i0 + 4], al3 = Tl[i1 + 4];
+                        const float av[4] = {Ts[i0], Ts[i1], Ts[i0 + 4], Ts[i1 + 4]};
+                        unsigned ah[4], al[4];
+                        split4(av, ah, al);
 #pragma unroll
                         for (int jn = 0; jn < 2; ++jn) {
-                            mma_tf32_raw(acc[im][jn], al0, al1, al2, al3, bh[jn][0], bh[jn][1]);
-                            mma_tf32_raw(acc[im][jn], ah0, ah1, ah2, ah3, bl[jn][0], bl[jn][1]);
-                            mma_tf32_raw(acc[im][jn], ah0, ah1, ah2, ah3, bh[jn][0], bh[jn][1]);
+                            mma_tf32_raw(acc[im][jn], al[0], al[1], al[2], al[3], bh[jn][0], bh[jn][1]);
+                            mma_tf32_raw(acc[im][jn], ah[0], ah[1], ah[2], ah[3], bl[jn][0], bl[jn][1]);
+                            mma_tf32_raw(acc[im][jn], ah[0], ah[1], ah[2], ah[3], bh[jn][0], bh[jn][1]);
                         }
                     }
                 }
@@ -370,10 +343,7 @@ __global__ void __launch_bounds__(128) q2_apply_tc_kernel(int n, int b, int S, c
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int a = im * 16 + gq + (q >> 1) * 8, col = jn * 8 + 2 * tq + (q & 1);
-                            unsigned hv, lv;
-                            split_tf32(-acc[im][jn][q], hv, lv);
-                            Yh[col * kWyTLd2 + a] = hv;
-                            Yl[col * kWyTLd2 + a] = lv;
+                            Y[col * kWyTLd2 + a] = -acc[im][jn][q];
                         }
             }
             __syncwarp();
@@ -381,6 +351,11 @@ __global__ void __launch_bounds__(128) q2_apply_tc_kernel(int n, int b, int S, c
             for (int mt = 0; mt < kWyRows / 16; ++mt) {
                 const int r = mt * 16;
                 if (r >= wrows) break;
+                // reflectors with a nonzero entry in rows r .. r + 15
+                const int alo = max(0, mA - 1 - min(r + 15, wrows - 1));
+                const int ahi = min(mA - 1, mA + b - 2 - r);
+                if (alo > ahi) continue;
+                const int k0lo = (alo / 8) * 8, k0hi = ahi + 1;
                 float acc[2][4];
 #pragma unroll
                 for (int jn = 0; jn < 2; ++jn) {
@@ -391,20 +366,21 @@ __global__ void __launch_bounds__(128) q2_apply_tc_kernel(int n, int b, int S, c
                     acc[jn][2] = (rb < wrows) ? rs(col, lo + rb) : 0.f;
                     acc[jn][3] = (rb < wrows) ? rs(col + 1, lo + rb) : 0.f;
                 }
-#pragma unroll
-                for (int k0 = 0; k0 < kWyM; k0 += 8) {
+                for (int k0 = k0lo; k0 < k0hi; k0 += 8) {
                     // A[row][a] = V[row][a] = Vt[a][row]
                     const int i0 = (k0 + tq) * kWyVLd + r + gq, i2 = (k0 + tq + 4) * kWyVLd + r + gq;
-                    unsigned ah0 = Vh[i0], ah1 = Vh[i0 + 8], ah2 = Vh[i2], ah3 = Vh[i2 + 8];
-                    unsigned al0 = Vl[i0], al1 = Vl[i0 + 8], al2 = Vl[i2], al3 = Vl[i2 + 8];
+                    const float av[4] = {Vs[i0], Vs[i0 + 8], Vs[i2], Vs[i2 + 8]};
+                    unsigned ah[4], al[4];
+                    split4(av, ah, al);
 #pragma unroll
                     for (int jn = 0; jn < 2; ++jn) {
                         const int col = jn * 8 + gq;
-                        unsigned bh0 = Yh[col * kWyTLd2 + k0 + tq], bh1 = Yh[col * kWyTLd2 + k0 + tq + 4];
-                        unsigned bl0 = Yl[col * kWyTLd2 + k0 + tq], bl1 = Yl[col * kWyTLd2 + k0 + tq + 4];
-                        mma_tf32_raw(acc[jn], al0, al1, al2, al3, bh0, bh1);
-                        mma_tf32_raw(acc[jn], ah0, ah1, ah2, ah3, bl0, bl1);
-                        mma_tf32_raw(acc[jn], ah0, ah1, ah2, ah3, bh0, bh1);
+                        unsigned bh0, bl0, bh1, bl1;
+                        split_tf32(Y[col * kWyTLd2 + k0 + tq], bh0, bl0);
+                        split_tf32(Y[col * kWyTLd2 + k0 + tq + 4], bh1, bl1);
+                        mma_tf32_raw(acc[jn], al[0], al[1], al[2], al[3], bh0, bh1);
+                        mma_tf32_raw(acc[jn], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+                        mma_tf32_raw(acc[jn], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
                     }
                 }
 #pragma unroll
@@ -454,8 +430,8 @@ cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const fl
     }
     EGB_COUNT_LAUNCH();
     q2_tfactor_kernel<<<nblk * S, 128, tsmem, st>>>(n, b, S, nblk, v2, tau2, tfac);
-    const size_t smem = (size_t)(kWyCols * kWyRingLd + 2 * kWyM * kWyVLd + 2 * kWyM * kWyTLd2 +
-                                 4 * 2 * kWyWcols * kWyTLd2) * sizeof(float);
+    const size_t smem = (size_t)(kWyCols * kWyRingLd + kWyM * kWyVLd + kWyM * kWyTLd2 +
+                                 kWyWarps * kWyWcols * kWyTLd2) * sizeof(float);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(q2_apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -464,7 +440,7 @@ cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const fl
     }
     (void)tau2;
     EGB_COUNT_LAUNCH();
-    q2_apply_tc_kernel<<<ceil_div(k, kWyCols), 128, smem, st>>>(n, b, S, tfac, k, z, ldz);
+    q2_apply_tc_kernel<<<ceil_div(k, kWyCols), 256, smem, st>>>(n, b, S, tfac, k, z, ldz);
     return cudaGetLastError();
 }
 

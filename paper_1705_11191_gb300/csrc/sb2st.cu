@@ -124,10 +124,9 @@ __device__ void two_sided(int L, T *D, int ldd, const T *v, T tau, T *p, T *red)
     T K = T(0.5) * tau * block_sum(part, red);
     for (int i = threadIdx.x; i < L; i += blockDim.x) p[i] -= K * v[i];  // q
     __syncthreads();
-    for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
-        int i = e % L, c = e / L;
-        D[i + c * ldd] = D[i + c * ldd] - v[i] * p[c] - p[i] * v[c];
-    }
+    const int i = threadIdx.x & 63;
+    if (i < L)
+        for (int c = threadIdx.x >> 6; c < L; c += 4) D[i + c * ldd] = D[i + c * ldd] - v[i] * p[c] - p[i] * v[c];
     __syncthreads();
 }
 
@@ -157,6 +156,7 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     T *vprev = vnew + b;         // b
     T *p = vprev + b;            // b
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int ti = tid & 63, tc = tid >> 6;  // element loops: row ti, columns tc, tc + 4, ...
     size_t slot = (size_t)j * a.S + t;
 
     if (t == 0) {
@@ -164,20 +164,16 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
         const int r0 = j + 1;
         for (int i = tid; i < b; i += nt) vnew[i] = (i < L) ? ldg_l2(band + (size_t)(1 + i) + (size_t)j * ldb) : T(0);
         // D = A[j+1 .. j+L]^2
-        for (int e = tid; e < L * L; e += nt) {
-            int i = e % L, c = e / L;
-            D[i + c * ld] = band_get(band, ldb, r0 + i, r0 + c);
-        }
+        if (ti < L)
+            for (int c = tc; c < L; c += 4) D[ti + c * ld] = band_get(band, ldb, r0 + ti, r0 + c);
         __syncthreads();
         T beta;
         T tau = house_smem<T>(L, vnew, red, &beta);
         for (int i = tid; i < L; i += nt)
             band[(size_t)(1 + i) + (size_t)j * ldb] = (i == 0) ? beta : T(0);
         two_sided<T>(L, D, ld, vnew, tau, p, red);
-        for (int e = tid; e < L * L; e += nt) {
-            int i = e % L, c = e / L;
-            if (i >= c) band[(size_t)(i - c) + (size_t)(r0 + c) * ldb] = D[i + c * ld];
-        }
+        if (ti < L)
+            for (int c = tc; c <= ti; c += 4) band[(size_t)(ti - c) + (size_t)(r0 + c) * ldb] = D[ti + c * ld];
         for (int i = tid; i < b; i += nt) v2[slot * b + i] = (i < L) ? vnew[i] : T(0);
         if (tid == 0) tau2[slot] = tau;
         __syncthreads();
@@ -190,23 +186,17 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     for (int i = tid; i < b; i += nt) vprev[i] = ldg_l2(v2 + pslot * b + i);
     const T taup = ldg_l2(tau2 + pslot);
     // X = A[r .. r+L-1, cb .. cb+b-1]  (all strictly below the diagonal, distance 1..2b-1)
-    for (int e = tid; e < L * b; e += nt) {
-        int i = e % L, c = e / L;
-        X[i + c * ld] = ldg_l2(band + (size_t)(r + i - (cb + c)) + (size_t)(cb + c) * ldb);
-    }
+    if (ti < L)
+        for (int c = tc; c < b; c += 4) X[ti + c * ld] = ldg_l2(band + (size_t)(r + ti - (cb + c)) + (size_t)(cb + c) * ldb);
     // D = A[r .. r+L-1]^2 (read now: the task's window is not touched by anyone else)
-    for (int e = tid; e < L * L; e += nt) {
-        int i = e % L, c = e / L;
-        D[i + c * ld] = band_get(band, ldb, r + i, r + c);
-    }
+    if (ti < L)
+        for (int c = tc; c < L; c += 4) D[ti + c * ld] = band_get(band, ldb, r + ti, r + c);
     __syncthreads();
     // X <- X H_prev : y = X v, X -= tau y v^T
     if (taup != T(0)) {
         rows_dot<T>(L, b, X, ld, vprev, taup, p);
-        for (int e = tid; e < L * b; e += nt) {
-            int i = e % L, c = e / L;
-            X[i + c * ld] = fma(-p[i], vprev[c], X[i + c * ld]);
-        }
+        if (ti < L)
+            for (int c = tc; c < b; c += 4) X[ti + c * ld] = fma(-p[ti], vprev[c], X[ti + c * ld]);
         __syncthreads();
     }
     // new reflector from X[:, 0]
@@ -217,33 +207,29 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     // left-apply to X[:, 1:]
     if (tau != T(0)) {
         cols_dot<T>(L, 1, b, X, ld, vnew, tau, p);
-        for (int e = tid; e < L * (b - 1); e += nt) {
-            int i = e % L, c = 1 + e / L;
-            X[i + c * ld] = fma(-vnew[i], p[c], X[i + c * ld]);
-        }
+        if (ti < L)
+            for (int c = 1 + tc; c < b; c += 4) X[ti + c * ld] = fma(-vnew[ti], p[c], X[ti + c * ld]);
         __syncthreads();
     }
     if (tid == 0) X[0] = beta;
     for (int i = 1 + tid; i < L; i += nt) X[i] = T(0);
     __syncthreads();
-    for (int e = tid; e < L * b; e += nt) {
-        int i = e % L, c = e / L;
-        band[(size_t)(r + i - (cb + c)) + (size_t)(cb + c) * ldb] = X[i + c * ld];
-    }
+    if (ti < L)
+        for (int c = tc; c < b; c += 4) band[(size_t)(r + ti - (cb + c)) + (size_t)(cb + c) * ldb] = X[ti + c * ld];
     two_sided<T>(L, D, ld, vnew, tau, p, red);
-    for (int e = tid; e < L * L; e += nt) {
-        int i = e % L, c = e / L;
-        if (i >= c) band[(size_t)(i - c) + (size_t)(r + c) * ldb] = D[i + c * ld];
-    }
+    if (ti < L)
+        for (int c = tc; c <= ti; c += 4) band[(size_t)(ti - c) + (size_t)(r + c) * ldb] = D[ti + c * ld];
     for (int i = tid; i < b; i += nt) v2[slot * b + i] = (i < L) ? vnew[i] : T(0);
     if (tid == 0) tau2[slot] = tau;
     __syncthreads();
 }
 
 // Persistent bulge chase with point-to-point ordering: CTA g runs sweeps g, g + G, ... in
-// order; step t of sweep j waits until sweep j-1 has finished step t+2 (or all its steps),
-// which (with the same rule for j-1) orders every pair of overlapping tasks as the
-// sequential algorithm does. progress[j] = number of finished steps of sweep j.
+// order; step t of sweep j waits until sweep j-1 has finished step t+1 (or all its steps).
+// Step t of sweep j touches rows and columns j+1+(t-1)b .. j+(t+1)b; among the tasks of
+// sweep j-1 only step t+1 (rows from j+(t+1)b) overlaps that window, and step t+2 starts
+// at row j+(t+2)b. With the same rule for j-1 this orders every pair of overlapping tasks
+// as the sequential algorithm does. progress[j] = number of finished steps of sweep j.
 template <typename T>
 __global__ void __launch_bounds__(256) chase_kernel(T *band, T *v2, T *tau2, ChaseArgs a, int *progress)
 {
@@ -259,7 +245,7 @@ __global__ void __launch_bounds__(256) chase_kernel(T *band, T *v2, T *tau2, Cha
         const int Sprev = (j > 0) ? (n - 2 - (j - 1)) / b + 1 : 0;
         for (int t = 0; t < Sj; ++t) {
             if (j > 0) {
-                const int need = min(t + 3, Sprev);
+                const int need = min(t + 2, Sprev);
                 if (threadIdx.x == 0) {
                     volatile int *pv = progress + (j - 1);
                     volatile int *vst = a.status;
@@ -320,8 +306,8 @@ cudaError_t sb2st(cudaStream_t st, int n, int b, T *band, int ldb, double *d, do
         }
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chase_kernel<T>, 256, smem);
-        int maxpar = (n - 2 + 2) / 3 + 1;  // upper bound of concurrently active sweeps
-        int conc = S / 3 + 2;
+        int maxpar = (n - 2 + 1) / 2 + 1;  // upper bound of concurrently active sweeps
+        int conc = S / 2 + 2;
         if (conc < maxpar) maxpar = conc;
         int G = per_sm * num_sms;
         if (G > maxpar) G = maxpar;
