@@ -7,8 +7,8 @@
 // X = A22 V T and W = X - (1/2) V (T^T (V^T X)).
 //
 // The panel QR is one cooperative launch: the m x b panel is split by rows over G CTAs,
-// each holding its rows in shared memory; per column there are two grid barriers
-// (norm, then the dot products of the reflector with the remaining columns). The
+// each holding its rows in shared memory; one grid barrier per column exchanges the
+// partial norm and the partial products of the column with the remaining columns. The
 // trailing update is GEMM work.
 #include <cooperative_groups.h>
 
@@ -21,9 +21,10 @@ struct PanelArgs {
     int m, bw, rows_per_cta;
     int lda, ldv;
     unsigned *count, *gen;  // grid barrier state (zeroed)
-    double *part;            // G partial norms
-    double *alpha;           // [bw] diagonal entries before reflection
-    double *wpart;           // G x bw partial dot products
+    double *part;            // 2 x gstride partial norms (by column parity)
+    double *alpha;           // 2 x 64: row j of the panel (by column parity)
+    double *wpart;           // 2 x gstride x 64 partial dot products (by column parity)
+    int gstride;             // >= G
     double *gram;            // G x bw x bw partial Gram matrices
     int *status;
 };
@@ -52,21 +53,54 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
     __syncthreads();
 
     const int nref = min(bw, a.m);
+    // One grid barrier per column. Before it, every CTA publishes (for column j, already
+    // updated by reflectors 0..j-1) the partial sum of squares below the diagonal and the
+    // unscaled partial dot products d_c = sum_{i>j} x_i P[i][c] (c > j); the CTA holding
+    // row j publishes that row. After it, every CTA forms the same reflector
+    // v = [1; x scl] and w_c = v . P_c = P[j][c] + scl d_c, and updates its rows. The
+    // published values alternate between two buffers by column parity: a CTA can be at
+    // most one column ahead of another.
     for (int j = 0; j < nref; ++j) {
-        // ---- phase A: partial sum of squares below the diagonal of column j
-        T ssT = T(0);
-        for (int i = tid; i < nrow; i += blockDim.x)
-            if (row0 + i > j) { T x = Ploc[i * bwp + j]; ssT = fma(x, x, ssT); }
-        double ss = block_sum((double)ssT, red);
-        if (tid == 0) {
-            a.part[g] = ss;
-            if (j >= row0 && j < row0 + nrow) a.alpha[j] = (double)Ploc[(j - row0) * bwp + j];
+        const int par = j & 1;
+        double *part = a.part + (size_t)par * a.gstride;              // [G]
+        double *dpart = a.wpart + (size_t)par * a.gstride * 64;       // [G][64]
+        double *prow = a.alpha + par * 64;                            // [64]
+        {
+            T ss = T(0), s = T(0);
+            const int c = tc;
+            for (int i = tid; i < nrow; i += blockDim.x)
+                if (row0 + i > j) { T x = Ploc[i * bwp + j]; ss = fma(x, x, ss); }
+            if (c > j && c < bw)
+                for (int i = tr; i < nrow; i += 4)
+                    if (row0 + i > j) s = fma(Ploc[i * bwp + j], Ploc[i * bwp + c], s);
+            colpart[tr][tc] = (double)s;
+            double sst = block_sum((double)ss, red);  // also orders colpart
+            if (tid < bw)
+                dpart[(size_t)g * 64 + tid] = colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
+            if (tid == 0) part[g] = sst;
+            if (j >= row0 && j < row0 + nrow && tid >= j && tid < bw)
+                prow[tid] = (double)Ploc[(j - row0) * bwp + tid];
         }
         if (!grid_barrier(a.count, a.gen, G, a.status)) return;
-        // ---- phase B: reflector of column j (every CTA computes the same numbers)
-        double sigma2 = 0.0;
-        for (int q = 0; q < G; ++q) sigma2 += ((volatile double *)a.part)[q];
-        double alpha = ((volatile double *)a.alpha)[j];
+        // ---- reflector of column j (every CTA computes the same numbers)
+        {
+            // sigma2 by warp 0; d_c by 64 column lanes x 4 row groups of CTAs
+            if (tid < 32) {
+                double v = 0.0;
+                for (int q = tid; q < G; q += 32) v += ((volatile double *)part)[q];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (tid == 0) red[0] = v;
+            }
+            double dv = 0.0;
+            if (tc > j && tc < bw)
+                for (int q = tr; q < G; q += 4) dv += ((volatile double *)dpart)[(size_t)q * 64 + tc];
+            colpart[tr][tc] = dv;
+            __syncthreads();
+            if (tid < bw) wsum[tid] = colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
+            __syncthreads();
+        }
+        const double sigma2 = red[0];
+        const double alpha = ((volatile double *)prow)[j];
         double beta, tau, scl;
         if (sigma2 == 0.0) { beta = alpha; tau = 0.0; scl = 0.0; }
         else {
@@ -75,50 +109,26 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             tau = (beta - alpha) / beta;
             scl = 1.0 / (alpha - beta);
         }
+        // w_c = P[j][c] + scl d_c; stored pre-multiplied by tau
+        if (tid > j && tid < bw) wsum[tid] = tau * (((volatile double *)prow)[tid] + scl * wsum[tid]);
+        __syncthreads();
         const T sclT = (T)scl;
         for (int i = tid; i < nrow; i += blockDim.x)
             if (row0 + i > j) Ploc[i * bwp + j] = Ploc[i * bwp + j] * sclT;
         __syncthreads();
-        // partial w_c = sum_i v_i P[i][c], c > j, over rows i >= j (v_j = 1)
         {
-            T s = T(0);
-            int c = tc;
+            const int c = tc;
             if (c > j && c < bw) {
+                const T wt = (T)wsum[c];
                 for (int i = tr; i < nrow; i += 4) {
-                    int gi = row0 + i;
+                    const int gi = row0 + i;
                     if (gi < j) continue;
-                    T v = (gi == j) ? T(1) : Ploc[i * bwp + j];
-                    s = fma(v, Ploc[i * bwp + c], s);
-                }
-            }
-            colpart[tr][tc] = (double)s;
-            __syncthreads();
-            if (tid < bw)
-                a.wpart[(size_t)g * bw + tid] =
-                    colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
-        }
-        if (tid == 0) tau_s[j] = tau;
-        if (!grid_barrier(a.count, a.gen, G, a.status)) return;
-        // ---- phase C: apply the reflector to the remaining columns
-        if (tid < bw) {
-            double w = 0.0;
-            if (tid > j)
-                for (int q = 0; q < G; ++q) w += ((volatile double *)a.wpart)[(size_t)q * bw + tid];
-            wsum[tid] = w;
-        }
-        __syncthreads();
-        {
-            int c = tc;
-            if (c > j && c < bw) {
-                const T wt = (T)(tau * wsum[c]);
-                for (int i = tr; i < nrow; i += 4) {
-                    int gi = row0 + i;
-                    if (gi < j) continue;
-                    T v = (gi == j) ? T(1) : Ploc[i * bwp + j];
+                    const T v = (gi == j) ? T(1) : Ploc[i * bwp + j];
                     Ploc[i * bwp + c] = fma(-v, wt, Ploc[i * bwp + c]);
                 }
             }
         }
+        if (tid == 0) tau_s[j] = tau;
         __syncthreads();
         if (tid == 0 && j >= row0 && j < row0 + nrow) Ploc[(j - row0) * bwp + j] = (T)beta;
         __syncthreads();
@@ -192,11 +202,11 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
     if (b > 64 || b < 1) return cudaErrorInvalidValue;
     // sync layout: [0..1] barrier words, then doubles
     double *dsync = reinterpret_cast<double *>(sync + 64);
-    const int max_g = 1024;
-    double *part = dsync;
-    double *alpha = part + max_g;
-    double *wpart = alpha + 64;
-    double *gram = wpart + (size_t)max_g * 64;
+    const int max_g = 512;
+    double *part = dsync;                           // 2 x max_g
+    double *alpha = part + 2 * max_g;               // 2 x 64
+    double *wpart = alpha + 128;                    // 2 x max_g x 64
+    double *gram = wpart + 2 * (size_t)max_g * 64;  // max_g x 64 x 64
 
     int dev = 0;
     cudaGetDevice(&dev);
@@ -204,8 +214,10 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         const int r0 = c0 + b;
         const int m = n - r0;
         const int bw = b;
-        // rows per CTA: at most 128, and enough CTAs to be co-resident
-        int rows = 128;
+        // rows per CTA: 256 (fewer CTAs make the per-column barrier and the reductions of
+        // the partials cheaper; the per-column work of a CTA stays small), more if needed
+        // for co-residency
+        int rows = 256;
         int G = ceil_div(m, rows);
         size_t smem = (size_t)rows * (bw + 1) * sizeof(T);
         size_t smem_t = 2 * (size_t)bw * bw * sizeof(double);
@@ -234,6 +246,7 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         pa.m = m; pa.bw = bw; pa.rows_per_cta = rows; pa.lda = lda; pa.ldv = n;
         pa.count = sync; pa.gen = sync + 1;
         pa.part = part; pa.alpha = alpha; pa.wpart = wpart; pa.gram = gram; pa.status = status;
+        pa.gstride = max_g;
         T *P = a + r0 + (size_t)c0 * lda;
         T *V = v1 + r0 + (size_t)c0 * n;
         T *Tm = t1 + (size_t)c0 * b;
