@@ -374,3 +374,54 @@ def ev_adjoint(ev, c, ev_bar=None, c_bar=None, guard: float = 1e-10):
     hb = c @ (0.5 * (xh + xh.T)) @ c.T
     sb = c @ (0.5 * (xs + xs.T)) @ c.T
     return hb, sb
+
+
+SING_FILL = np.finfo(np.float64).max  # eigenvalue slots of dropped basis directions
+
+
+def canonical_transform(s, tau: float, force: bool = False):
+    """Singularity check of the overlap matrix (sec. 4.4, Eq. 10): all eigenvalues of S by
+    Jacobi; when one or more are below tau (or force), S = X X^T with X = x sqrt(lambda) and
+    the eigenvectors with lambda < tau dropped, which gives the transformation
+    U = x_k lambda_k^{-1/2} (n x N_nonsing): H~ = U^T H U and c = U c~.
+    Returns (U or None when S is not singular and not force, eigenvalues of S)."""
+    w, v, _ = jacobi(s)
+    keep = w >= tau
+    if keep.all() and not force:
+        return None, w
+    return np.asfortranarray(v[:, keep] / np.sqrt(w[keep])), w
+
+
+def solve_sing(h, s, n_state: int, n_el: float, *, tau: float = 1e-5, force: bool = False,
+               scheme: int = SCHEME_INTEGER, kt: float = 0.0, occ_accuracy: float = 1e-12,
+               mu_max_steps: int = 200, want_pw: bool = True):
+    """Whole path with the singularity check: the Cholesky route when S has no eigenvalue
+    below tau (and not force), else the reduced standard problem H~ = U^T H U of size
+    N_nonsing, eigenvectors c = U c~. eval has length n; the slots of the dropped
+    directions (l >= N_nonsing) hold SING_FILL."""
+    h = _f64(h)
+    n = h.shape[0]
+    u, ws = canonical_transform(s, tau, force)
+    if u is None:
+        r = solve(h, s, n_state, n_el, scheme=scheme, kt=kt, occ_accuracy=occ_accuracy,
+                  mu_max_steps=mu_max_steps, want_pw=want_pw)
+        r.update(n_nonsing=n, s_eval=ws)
+        return r
+    nn = u.shape[1]
+    k = int(n_state)
+    if k > nn:
+        raise OracleError("n_state exceeds the non-singular basis size")
+    ht = u.T @ h @ u
+    ht = 0.5 * (ht + ht.T)
+    w, z, _ = jacobi(ht)
+    c = np.asfortranarray(u @ z[:, :k])
+    ev = np.full(n, SING_FILL)
+    ev[:nn] = w
+    f, mu = occupation(w[:k], n_el, scheme=scheme, kt=kt, occ_accuracy=occ_accuracy,
+                       mu_max_steps=mu_max_steps)
+    out = dict(eval=ev, C=c, f=f, mu=mu, energy=float(np.sum(f * w[:k])), n_nonsing=nn,
+               s_eval=ws, P=None, W=None)
+    if want_pw:
+        out["P"] = weighted_outer(c, f)
+        out["W"] = weighted_outer(c, f * w[:k])
+    return out
