@@ -157,6 +157,24 @@ int elsi_get_refine_info(elsi_handle h, int *iters, double *orth_err);
 int elsi_density_noalloc(int n_basis, int n_state, const double *evec, const double *occ,
                          const double *eval, double *den_mat, double *edm, void *stream);
 
+/* Singularity check of the overlap matrix (sec. 4.4, Eq. 10; the customisation keywords
+ * no_singularity_check and singularity_tolerance of sec. 4.5). mode 0 (default): no
+ * check, S is factorised by Cholesky. mode 1: all eigenvalues of S are computed; if one
+ * or more are below tau, S = X X^T with X = x sqrt(lambda), the eigenvectors of the
+ * eigenvalues below tau are dropped and the problem is solved in the N_nonsing remaining
+ * directions (H~ = U^T H U with U = x_k lambda_k^{-1/2}, c = U c~); otherwise the
+ * Cholesky route is used. mode 2: the eigendecomposition transformation always (the
+ * check still drops eigenvalues below tau). The check costs one binary64 eigensolve of
+ * S; it is repeated on every call unless elsi_set_reuse_ovlp_factor is set. Real
+ * problems only (the complex and batched entry points ignore the setting). With a
+ * reduced basis, eval[l] = DBL_MAX for l >= N_nonsing and n_state must not exceed
+ * N_nonsing (ELSI_ERR_ARG); a solve where every eigenvalue is below tau returns
+ * ELSI_ERR_NOT_PD. tau > 0 (default 1e-5), else ELSI_ERR_ARG. */
+int elsi_set_sing_check(elsi_handle h, int mode);
+int elsi_set_sing_tol(elsi_handle h, double tau);
+/* N_nonsing of the last real solve (n_basis when no direction was dropped). */
+int elsi_get_n_nonsing(elsi_handle h, int *n_nonsing);
+
 /* -kT S_ent of the last elsi_dm_real / elsi_dm_complex call (host scalar, <= 0): the
  * entropy term of the free energy F = E_band - kT S_ent that is stationary in the
  * occupations at fixed electron count, S_ent = -g sum_l [phi ln phi + (1-phi) ln(1-phi)]

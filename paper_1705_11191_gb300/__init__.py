@@ -81,6 +81,9 @@ def _declare(lib):
         "elsi_occupation_weighted": ([H, i, _vp, _vp, d, _vp, _dp], i),
         "elsi_batch_dm": ([H, _vp, _pp, _pp, _dp], i),
         "elsi_get_entropy": ([H, _dp], i),
+        "elsi_set_sing_check": ([H, i], i),
+        "elsi_set_sing_tol": ([H, d], i),
+        "elsi_get_n_nonsing": ([H, _ip], i),
         "elsi_dm_adjoint_real": ([H, i, d, _vp, _vp, _vp, _vp], i),
         "elsi_ev_adjoint_real": ([H, i, i, _vp, _vp, _vp, _vp, _vp, _vp], i),
     }
@@ -301,6 +304,17 @@ class Handle:
                                          _vp(hp(edm)), ctypes.byref(e))
         self._check(rc, "elsi_dm_real_host")
         return e.value
+
+    def set_sing_check(self, mode: int, tol: float | None = None):
+        """Singularity check of S (0 off, 1 check, 2 always transform) and its tolerance."""
+        self._check(self._lib.elsi_set_sing_check(self._h, int(mode)), "elsi_set_sing_check")
+        if tol is not None:
+            self._check(self._lib.elsi_set_sing_tol(self._h, float(tol)), "elsi_set_sing_tol")
+
+    def get_n_nonsing(self) -> int:
+        v = ctypes.c_int(0)
+        self._check(self._lib.elsi_get_n_nonsing(self._h, ctypes.byref(v)), "elsi_get_n_nonsing")
+        return v.value
 
     def get_entropy(self) -> float:
         """-kT S_ent of the last density-matrix solve (F = E_band + this)."""

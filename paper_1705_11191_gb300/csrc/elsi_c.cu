@@ -87,6 +87,7 @@ int elsi_finalize(elsi_handle *hp)
     elsi_gb_handle_s *h = *hp;
     free_complex(h);
     free_batch(h);
+    free_sing(h);
     free_workspace(h);
     h->magic = 0;
     delete h;
@@ -219,6 +220,33 @@ int elsi_get_edm_complex(elsi_handle h, double *edm)
     if (check_handle(h)) return ELSI_ERR_STATE;
     if (!edm) return set_error(h, ELSI_ERR_ARG, "null pointer argument");
     return get_edm_complex(h, edm);
+}
+
+int elsi_set_sing_check(elsi_handle h, int mode)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (mode < 0 || mode > 2) return set_error(h, ELSI_ERR_ARG, "singularity-check mode %d", mode);
+    h->sing_mode = mode;
+    h->have_l = false;
+    sing_invalidate(h);
+    return ELSI_OK;
+}
+
+int elsi_set_sing_tol(elsi_handle h, double tau)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!(tau > 0.0)) return set_error(h, ELSI_ERR_ARG, "singularity tolerance %g", tau);
+    h->sing_tol = tau;
+    sing_invalidate(h);
+    return ELSI_OK;
+}
+
+int elsi_get_n_nonsing(elsi_handle h, int *n_nonsing)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!n_nonsing) return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    *n_nonsing = h->n_nonsing > 0 ? h->n_nonsing : h->n;
+    return ELSI_OK;
 }
 
 int elsi_get_entropy(elsi_handle h, double *ts)

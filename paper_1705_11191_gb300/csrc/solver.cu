@@ -30,7 +30,7 @@ void free_workspace(elsi_gb_handle_s *h)
         return set_error(h, ELSI_ERR_NOMEM, "cannot allocate %s (%zu bytes)", #name,       \
                          sizeof(type) * (size_t)(count));
 
-static int ensure_workspace(elsi_gb_handle_s *h, int kz)
+int ensure_workspace(elsi_gb_handle_s *h, int kz)
 {
     Workspace &w = h->wk;
     const size_t n = h->n;
@@ -184,6 +184,15 @@ static int solve_fp64(elsi_gb_handle_s *h, const SolveRequest &rq)
 int run_solve(elsi_gb_handle_s *h, const SolveRequest &rq)
 {
     h->last_error.clear();
+    h->n_nonsing = h->n;
+    if (h->sing_mode != 0 && !h->overlap_is_unit && rq.ovlp) {
+        // singularity check of S (sec. 4.4): a singular S is handled by the eigendecomposition
+        // transformation of Eq. 10 instead of the Cholesky factorisation
+        bool active = false;
+        int rc = sing_prepare(h, rq.ovlp, &active);
+        if (rc) return rc;
+        if (active) return solve_singular(h, rq);
+    }
     const bool ev_mode = rq.evec != nullptr;
     int kz = h->n_state;
     if (h->precision == ELSI_PREC_FP32_REFINE) kz = h->n;

@@ -59,6 +59,7 @@ struct Workspace {
 };
 
 struct BatchState;
+struct SingState;
 
 }  // namespace egb
 
@@ -94,6 +95,12 @@ struct elsi_gb_handle_s {
     bool have_cedm = false;
     // several independent problems (k-points / spin channels): batch.cu
     egb::BatchState *batch = nullptr;
+    // singularity check of the overlap (sec. 4.4): sing.cu. sing_mode 0 = off, 1 = check,
+    // 2 = always transform by the eigendecomposition of S
+    int sing_mode = 0;
+    double sing_tol = 1e-5;
+    int n_nonsing = 0;
+    egb::SingState *sing = nullptr;
 };
 
 namespace egb {
@@ -110,6 +117,11 @@ struct SolveRequest {
 int set_error(elsi_gb_handle_s *h, int code, const char *fmt, ...);
 bool ensure_buf(void **p, size_t *cap, size_t bytes);
 int run_solve(elsi_gb_handle_s *h, const SolveRequest &rq);
+int ensure_workspace(elsi_gb_handle_s *h, int kz);
+int sing_prepare(elsi_gb_handle_s *h, const double *ovlp, bool *active);
+int solve_singular(elsi_gb_handle_s *h, const SolveRequest &rq);
+void free_sing(elsi_gb_handle_s *h);
+void sing_invalidate(elsi_gb_handle_s *h);  // forget the transformation decision
 void free_workspace(elsi_gb_handle_s *h);
 int solve_complex(elsi_gb_handle_s *h, const double *ham, const double *ovlp, double *eval,
                   double *evec, double *den_mat, double *energy);
