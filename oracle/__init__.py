@@ -143,6 +143,7 @@ def back_substitute(l, vt, k: int | None = None):
 
 
 SCHEME_INTEGER, SCHEME_GAUSSIAN, SCHEME_FERMI = 0, 1, 2
+SCHEME_MP0, SCHEME_MP1 = 3, 4  # Methfessel-Paxton of order 0 (= Gaussian) and 1
 
 
 def occupation(eps, n_el: float, scheme: int = SCHEME_INTEGER, kt: float = 0.0,
@@ -310,7 +311,10 @@ def entropy_term(eps, f, mu: float, scheme: int, kt: float) -> float:
     (the paper names the broadening schemes, sec. 4.4, but gives no entropy; this is the
     term for which dF/deps_l = f_l at fixed electron count, so that dF/dH = P):
       Fermi-Dirac: S_ent = -g sum_l [phi ln phi + (1 - phi) ln(1 - phi)], phi = f_l / g;
-      Gaussian:    S_ent = g sum_l exp(-x_l^2) / (2 sqrt(pi)), x_l = (eps_l - mu) / kT;
+      Gaussian and Methfessel-Paxton order 0:
+                   S_ent = g sum_l exp(-x_l^2) / (2 sqrt(pi)), x_l = (eps_l - mu) / kT;
+      Methfessel-Paxton order 1 (Phys. Rev. B 40, 3616 (1989)):
+                   S_ent = g sum_l (1/2) A_1 H_2(x_l) exp(-x_l^2);
       integer:     0."""
     g = 2.0
     eps = np.asarray(eps, dtype=float)
@@ -325,6 +329,11 @@ def entropy_term(eps, f, mu: float, scheme: int, kt: float) -> float:
                 s += p * np.log(p) + (1.0 - p) * np.log1p(-p)
         return float(kt * g * s)
     x = (eps - mu) / kt
+    if scheme == SCHEME_MP1:
+        # Methfessel-Paxton order N: S_ent = g sum_l (1/2) A_N H_{2N}(x_l) exp(-x_l^2);
+        # N = 1: A_1 = -1 / (4 sqrt(pi)), H_2(x) = 4 x^2 - 2
+        s_l = 0.5 * (-1.0 / (4.0 * np.sqrt(np.pi))) * (4.0 * x * x - 2.0) * np.exp(-x * x)
+        return float(-kt * g * np.sum(s_l))
     return float(-kt * g * np.sum(np.exp(-x * x)) / (2.0 * np.sqrt(np.pi)))
 
 

@@ -21,6 +21,7 @@
  * generalized chain closed form, 2x2 quadratic, brute force against LAPACK on small
  * cases, and the invariants Tr(PS)=N_el, PSP=2P, Tr(PH)=Tr(WS)=sum f*eps.
  */
+#define _DEFAULT_SOURCE
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -252,9 +253,16 @@ void orc_back_substitute(int n, int k, const double *l, const double *vt, double
  * highest occupied state downwards (each f clamped at 0), so sum f = n_el exactly.
  * Returns 0, or -1 for invalid arguments / an unreachable electron count.
  * ---------------------------------------------------------------------------------- */
+/* Occupation fraction for x = (eps - mu) / kT. Schemes (sec. 4.5, broadening_scheme):
+ * 1 Gaussian, 0.5 erfc(x); 2 Fermi-Dirac (Eq. 14); 3 Methfessel-Paxton of order 0 (the
+ * Gaussian); 4 Methfessel-Paxton of order 1 (Methfessel & Paxton, Phys. Rev. B 40, 3616
+ * (1989): S_N(x) = 0.5 erfc(x) + sum_{n=1..N} A_n H_{2n-1}(x) exp(-x^2),
+ * A_n = (-1)^n / (n! 4^n sqrt(pi)), H the physicists' Hermite polynomials; for N = 1,
+ * A_1 H_1(x) = -x / (2 sqrt(pi))). */
 static double occ_phi(int scheme, double x)
 {
-    if (scheme == 1) return 0.5 * (1.0 - erf(x));
+    if (scheme == 1 || scheme == 3) return 0.5 * erfc(x);
+    if (scheme == 4) return 0.5 * erfc(x) - x * exp(-x * x) / (2.0 * sqrt(M_PI));
     /* Fermi-Dirac in a form that does not overflow */
     if (x > 0.0) { double e = exp(-x); return e / (1.0 + e); }
     return 1.0 / (1.0 + exp(x));
@@ -285,7 +293,7 @@ int orc_occupation(int k, const double *eps, double n_el, int scheme, double kt,
         *mu_out = eps[top];
         return 0;
     }
-    if (!(kt > 0.0) || (scheme != 1 && scheme != 2)) return -1;
+    if (!(kt > 0.0) || scheme < 1 || scheme > 4) return -1;
     double lo = eps[0], hi = eps[k - 1];
     for (int it = 0; it < 1000 && occ_count(k, eps, scheme, kt, lo, g) > n_el; ++it) lo -= 1.0;
     for (int it = 0; it < 1000 && occ_count(k, eps, scheme, kt, hi, g) < n_el; ++it) hi += 1.0;
@@ -381,7 +389,7 @@ int orc_occupation_weighted(int m, const double *eps, const double *wt, double n
         free(ord);
         return 0;
     }
-    if (!(kt > 0.0) || (scheme != 1 && scheme != 2)) { free(ord); return -1; }
+    if (!(kt > 0.0) || scheme < 1 || scheme > 4) { free(ord); return -1; }
     double lo = eps[ord[0]], hi = eps[ord[m - 1]];
     for (int it = 0; it < 1000 && wocc_count(m, eps, wt, scheme, kt, lo, g) > n_el; ++it) lo -= 1.0;
     for (int it = 0; it < 1000 && wocc_count(m, eps, wt, scheme, kt, hi, g) < n_el; ++it) hi += 1.0;
