@@ -52,11 +52,16 @@ extern "C" {
 #define ELSI_MODE_SINGLE_PROC 2
 
 /* Broadening schemes (elsi_customize_mu, sec. 4.5). 0 is this library's addition:
- * integer (aufbau) occupation without broadening. 3 and 4 (Methfessel-Paxton) are
- * named by the paper without a formula and return ELSI_ERR_UNSUPPORTED. */
+ * integer (aufbau) occupation without broadening. 3 and 4 are the Methfessel-Paxton
+ * schemes of order 0 and 1 that the paper names; their formulas (occupation
+ * 0.5 erfc(x) + sum_n A_n H_{2n-1}(x) exp(-x^2), entropy term (1/2) A_N H_{2N}(x)
+ * exp(-x^2)) are those of the original publication. Order-1 occupations may fall
+ * slightly outside [0, 2]. */
 #define ELSI_OCC_INTEGER 0
 #define ELSI_OCC_GAUSSIAN 1
 #define ELSI_OCC_FERMI 2
+#define ELSI_OCC_MP0 3   /* Methfessel-Paxton order 0 (the Gaussian scheme) */
+#define ELSI_OCC_MP1 4   /* Methfessel-Paxton order 1 (Phys. Rev. B 40, 3616 (1989)) */
 
 /* Arithmetic of the reduction and back-transformations. */
 #define ELSI_PREC_FP64 0        /* every stage in binary64 */

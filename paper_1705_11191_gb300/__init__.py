@@ -17,13 +17,14 @@ import threading
 
 __all__ = ["load", "Handle", "ElsiError", "solve_dm", "solve_ev", "STAGES",
            "SOLVER_ELPA", "FORMAT_DENSE", "MODE_SINGLE_PROC", "OCC_INTEGER",
-           "OCC_GAUSSIAN", "OCC_FERMI", "PREC_FP64", "PREC_FP32_REFINE", "LIB_PATH"]
+           "OCC_GAUSSIAN", "OCC_FERMI", "OCC_MP0", "OCC_MP1", "PREC_FP64", "PREC_FP32_REFINE", "LIB_PATH"]
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libelsi_gb.so")
 
 SOLVER_ELPA, FORMAT_DENSE, MODE_MULTI_PROC, MODE_SINGLE_PROC = 1, 1, 1, 2
 OCC_INTEGER, OCC_GAUSSIAN, OCC_FERMI = 0, 1, 2
+OCC_MP0, OCC_MP1 = 3, 4  # Methfessel-Paxton of order 0 (= Gaussian) and 1
 PREC_FP64, PREC_FP32_REFINE = 0, 1
 
 ERR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_UNSUPPORTED", 3: "ERR_NOT_PD",

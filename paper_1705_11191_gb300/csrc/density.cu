@@ -8,9 +8,14 @@
 
 namespace egb {
 
+// Occupation fraction for x = (eps - mu) / kT: Gaussian and Methfessel-Paxton order 0,
+// 0.5 erfc(x); Methfessel-Paxton order 1 (Phys. Rev. B 40, 3616 (1989)),
+// 0.5 erfc(x) + A_1 H_1(x) exp(-x^2) = 0.5 erfc(x) - x exp(-x^2) / (2 sqrt(pi));
+// Fermi-Dirac (Eq. 14) otherwise.
 __device__ __forceinline__ double occ_phi(int scheme, double x)
 {
-    if (scheme == ELSI_OCC_GAUSSIAN) return 0.5 * (1.0 - erf(x));
+    if (scheme == ELSI_OCC_GAUSSIAN || scheme == ELSI_OCC_MP0) return 0.5 * erfc(x);
+    if (scheme == ELSI_OCC_MP1) return 0.5 * erfc(x) - x * exp(-x * x) * 0.28209479177387814347;
     if (x > 0.0) { double e = exp(-x); return e / (1.0 + e); }
     return 1.0 / (1.0 + exp(x));
 }
@@ -18,10 +23,14 @@ __device__ __forceinline__ double occ_phi(int scheme, double x)
 // Per-state entropy summand s with -kT S_ent = kT g sum s, the term that makes the free
 // energy E_band - kT S_ent stationary in the occupations at fixed electron count:
 // Fermi-Dirac s = phi ln phi + (1 - phi) ln(1 - phi) (phi = f / g);
-// Gaussian s = -exp(-x^2) / (2 sqrt(pi)) (x = (eps - mu) / kT).
+// Gaussian s = -exp(-x^2) / (2 sqrt(pi)) (x = (eps - mu) / kT); Methfessel-Paxton order 1
+// s = -(1/2) A_1 H_2(x) exp(-x^2).
 __device__ __forceinline__ double occ_entropy(int scheme, double phi, double x)
 {
-    if (scheme == ELSI_OCC_GAUSSIAN) return -exp(-x * x) * 0.28209479177387814347;  // 1 / (2 sqrt(pi))
+    // 0.28209... = 1 / (2 sqrt(pi))
+    if (scheme == ELSI_OCC_GAUSSIAN || scheme == ELSI_OCC_MP0) return -exp(-x * x) * 0.28209479177387814347;
+    // Methfessel-Paxton order 1: -(1/2) A_1 H_2(x) exp(-x^2) = (2 x^2 - 1) exp(-x^2) / (4 sqrt(pi))
+    if (scheme == ELSI_OCC_MP1) return (2.0 * x * x - 1.0) * exp(-x * x) * 0.14104739588693907174;
     if (!(phi > 0.0 && phi < 1.0)) return 0.0;
     return phi * log(phi) + (1.0 - phi) * log1p(-phi);
 }

@@ -106,9 +106,7 @@ int elsi_set_overlap_is_unit(elsi_handle h, int v)
 int elsi_set_broadening_scheme(elsi_handle h, int s)
 {
     if (check_handle(h)) return ELSI_ERR_STATE;
-    if (s == 3 || s == 4)
-        return set_error(h, ELSI_ERR_UNSUPPORTED, "Methfessel-Paxton broadening is not provided");
-    if (s < 0 || s > 2) return set_error(h, ELSI_ERR_ARG, "broadening scheme %d", s);
+    if (s < 0 || s > 4) return set_error(h, ELSI_ERR_ARG, "broadening scheme %d", s);
     h->scheme = s;
     return ELSI_OK;
 }

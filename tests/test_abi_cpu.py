@@ -49,9 +49,10 @@ def test_handle_lifecycle_and_setters(lib):
     h.set_occ_accuracy(1e-10)
     h.set_mu_max_steps(50)
     h.set_precision(egb.PREC_FP32_REFINE)
+    h.set_broadening(egb.OCC_MP1, 0.01)  # Methfessel-Paxton order 1
     with pytest.raises(egb.ElsiError) as e:
-        h.set_broadening(3)  # Methfessel-Paxton
-    assert e.value.code == 2
+        h.set_broadening(5)
+    assert e.value.code == 1
     with pytest.raises(egb.ElsiError):
         h.set_band_width(7)
     with pytest.raises(egb.ElsiError) as e:
