@@ -162,6 +162,29 @@ int elsi_get_refine_info(elsi_handle h, int *iters, double *orth_err);
 int elsi_density_noalloc(int n_basis, int n_state, const double *evec, const double *occ,
                          const double *eval, double *den_mat, double *edm, void *stream);
 
+/* ---- Sparse input: the PEXSI_CSC format (sec. 3.2, Fig. 2; elsi_set_csc and the
+ * _sparse entry points of sec. 4.3-4.4) -----------------------------------------------
+ * On one GPU the whole n_basis x n_basis matrix is one compressed-sparse-column block:
+ * nnz values, row_idx (nnz row indices) and col_ptr (n_basis + 1 column starts, the last
+ * equal to nnz), with indices counted from index_base (0, or 1 as in the paper's Fortran
+ * examples). The pattern holds both triangles of the symmetric H and S (one pattern for
+ * both). row_idx and col_ptr may be host or device pointers; they are copied into the
+ * handle and checked (ELSI_ERR_ARG on an index out of range or a decreasing col_ptr).
+ * elsi_ev_real_sparse: ham, ovlp = device arrays of the nnz values; eval (n_basis) and
+ *   evec (n_basis x n_state, dense, column-major) as for elsi_ev_real (the eigenvectors
+ *   are not sparse).
+ * elsi_dm_real_sparse: den_mat = device array of nnz values, the density matrix P at the
+ *   pattern's positions; energy as for elsi_dm_real.
+ * elsi_get_edm_real_sparse: W of the last sparse density-matrix call at the pattern.
+ * The solve itself is the dense path (the matrices are scattered into dense storage on
+ * the device). ELSI_ERR_STATE without a pattern. */
+int elsi_set_csc(elsi_handle h, int nnz, const int *row_idx, const int *col_ptr, int index_base);
+int elsi_ev_real_sparse(elsi_handle h, const double *ham, const double *ovlp, double *eval,
+                        double *evec);
+int elsi_dm_real_sparse(elsi_handle h, const double *ham, const double *ovlp, double *den_mat,
+                        double *energy);
+int elsi_get_edm_real_sparse(elsi_handle h, double *edm);
+
 /* Singularity check of the overlap matrix (sec. 4.4, Eq. 10; the customisation keywords
  * no_singularity_check and singularity_tolerance of sec. 4.5). mode 0 (default): no
  * check, S is factorised by Cholesky. mode 1: all eigenvalues of S are computed; if one

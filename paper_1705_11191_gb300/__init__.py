@@ -83,6 +83,10 @@ def _declare(lib):
         "elsi_batch_dm": ([H, _vp, _pp, _pp, _dp], i),
         "elsi_get_entropy": ([H, _dp], i),
         "elsi_set_sing_check": ([H, i], i),
+        "elsi_set_csc": ([H, i, _vp, _vp, i], i),
+        "elsi_ev_real_sparse": ([H, _vp, _vp, _vp, _vp], i),
+        "elsi_dm_real_sparse": ([H, _vp, _vp, _vp, _dp], i),
+        "elsi_get_edm_real_sparse": ([H, _vp], i),
         "elsi_set_sing_tol": ([H, d], i),
         "elsi_get_n_nonsing": ([H, _ip], i),
         "elsi_dm_adjoint_real": ([H, i, d, _vp, _vp, _vp, _vp], i),
@@ -305,6 +309,47 @@ class Handle:
                                          _vp(hp(edm)), ctypes.byref(e))
         self._check(rc, "elsi_dm_real_host")
         return e.value
+
+    # ---- sparse (CSC) input
+    def set_csc(self, row_idx, col_ptr, index_base: int = 0):
+        """CSC pattern of H and S: int32 tensors (CUDA or CPU) of nnz row indices and n + 1
+        column starts."""
+        import torch
+        def ip(t):
+            if t.dtype != torch.int32 or not t.is_contiguous():
+                raise ValueError("expected a contiguous int32 tensor")
+            return t.data_ptr()
+        self._csc_nnz = int(row_idx.numel())
+        rc = self._lib.elsi_set_csc(self._h, self._csc_nnz, _vp(ip(row_idx)), _vp(ip(col_ptr)),
+                                    int(index_base))
+        self._check(rc, "elsi_set_csc")
+
+    def ev_real_sparse(self, hval, sval=None):
+        import torch
+        ev = torch.empty(self.n, dtype=torch.float64, device=hval.device)
+        vec = torch.empty((self.n_state, self.n), dtype=torch.float64, device=hval.device)
+        rc = self._lib.elsi_ev_real_sparse(self._h, _vp(_ptr(hval)),
+                                           _vp(_ptr(sval) if sval is not None else None),
+                                           _vp(_ptr(ev)), _vp(_ptr(vec)))
+        self._check(rc, "elsi_ev_real_sparse")
+        return ev, vec.t()
+
+    def dm_real_sparse(self, hval, sval=None):
+        """Returns (P at the pattern (nnz values), band energy)."""
+        import torch
+        p = torch.empty_like(hval)
+        e = ctypes.c_double(0.0)
+        rc = self._lib.elsi_dm_real_sparse(self._h, _vp(_ptr(hval)),
+                                           _vp(_ptr(sval) if sval is not None else None),
+                                           _vp(_ptr(p)), ctypes.byref(e))
+        self._check(rc, "elsi_dm_real_sparse")
+        return p, e.value
+
+    def get_edm_sparse(self):
+        import torch
+        w = torch.empty(self._csc_nnz, dtype=torch.float64, device="cuda")
+        self._check(self._lib.elsi_get_edm_real_sparse(self._h, _vp(_ptr(w))), "elsi_get_edm_real_sparse")
+        return w
 
     def set_sing_check(self, mode: int, tol: float | None = None):
         """Singularity check of S (0 off, 1 check, 2 always transform) and its tolerance."""

@@ -220,6 +220,37 @@ int elsi_get_edm_complex(elsi_handle h, double *edm)
     return get_edm_complex(h, edm);
 }
 
+int elsi_set_csc(elsi_handle h, int nnz, const int *row_idx, const int *col_ptr, int index_base)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    return csc_set(h, nnz, row_idx, col_ptr, index_base);
+}
+
+int elsi_ev_real_sparse(elsi_handle h, const double *ham, const double *ovlp, double *eval,
+                        double *evec)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!ham || !eval || !evec || (!ovlp && !h->overlap_is_unit))
+        return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    return csc_solve(h, ham, ovlp, eval, evec, nullptr, nullptr);
+}
+
+int elsi_dm_real_sparse(elsi_handle h, const double *ham, const double *ovlp, double *den_mat,
+                        double *energy)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!ham || !den_mat || (!ovlp && !h->overlap_is_unit))
+        return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    return csc_solve(h, ham, ovlp, nullptr, nullptr, den_mat, energy);
+}
+
+int elsi_get_edm_real_sparse(elsi_handle h, double *edm)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!edm) return set_error(h, ELSI_ERR_ARG, "null pointer argument");
+    return csc_get_edm(h, edm);
+}
+
 int elsi_set_sing_check(elsi_handle h, int mode)
 {
     if (check_handle(h)) return ELSI_ERR_STATE;

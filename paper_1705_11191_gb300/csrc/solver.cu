@@ -15,7 +15,7 @@ void free_workspace(elsi_gb_handle_s *h)
     Workspace &w = h->wk;
     void *bufs[] = {w.a, w.l, w.v1, w.edm, w.v2, w.tau2, w.band, w.t1, w.invd, w.work, w.z,
                     w.d, w.e, w.w, w.f, w.scal, w.stein, w.rf, w.oz, w.ozexp, w.q2f, w.sync, w.status,
-                    w.host_h, w.host_s, w.host_p, w.adj, w.tcw};
+                    w.host_h, w.host_s, w.host_p, w.adj, w.tcw, w.csc_row, w.csc_col, w.csc_status};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (w.status_host) cudaFreeHost(w.status_host);

@@ -51,6 +51,9 @@ struct Workspace {
     EGB_BUF(double, host_p)
     EGB_BUF(double, rfc)     // complex route: real eigenpair staging
     EGB_BUF(double, adj)     // eigenpair adjoint scratch
+    EGB_BUF(int, csc_row)    // CSC pattern (base 0): row indices
+    EGB_BUF(int, csc_col)    // CSC pattern: column pointers (n + 1)
+    EGB_BUF(int, csc_status)
 #undef EGB_BUF
     int *status_host = nullptr;  // pinned
     double *scal_host = nullptr; // pinned
@@ -100,6 +103,7 @@ struct elsi_gb_handle_s {
     int sing_mode = 0;
     double sing_tol = 1e-5;
     int n_nonsing = 0;
+    int csc_nnz = -1;  // non-zeros of the CSC pattern set by elsi_set_csc (-1: none)
     egb::SingState *sing = nullptr;
 };
 
@@ -121,6 +125,10 @@ int ensure_workspace(elsi_gb_handle_s *h, int kz);
 int sing_prepare(elsi_gb_handle_s *h, const double *ovlp, bool *active);
 int solve_singular(elsi_gb_handle_s *h, const SolveRequest &rq);
 void free_sing(elsi_gb_handle_s *h);
+int csc_set(elsi_gb_handle_s *h, int nnz, const int *row_idx, const int *col_ptr, int base);
+int csc_solve(elsi_gb_handle_s *h, const double *hval, const double *sval, double *eval,
+              double *evec, double *dm_val, double *energy);
+int csc_get_edm(elsi_gb_handle_s *h, double *edm_val);
 void sing_invalidate(elsi_gb_handle_s *h);  // forget the transformation decision
 void free_workspace(elsi_gb_handle_s *h);
 int solve_complex(elsi_gb_handle_s *h, const double *ham, const double *ovlp, double *eval,
