@@ -88,6 +88,11 @@ int elsi_set_mu_max_steps(elsi_handle h, int mu_max_steps);
 /* Additions of this library (no counterpart in the paper's keyword list): */
 int elsi_set_precision(elsi_handle h, int precision);      /* ELSI_PREC_* */
 int elsi_set_band_width(elsi_handle h, int band_width);    /* 8..128, multiple of 8 */
+/* elsi_customize_elpa, keyword elpa_solver (sec. 4.5): 1 = one-stage tridiagonalisation
+ * T = Q^T H~ Q (Eq. 11, first form; blocked Householder with a matrix-vector product per
+ * column, memory-bound), 2 = two-stage full -> band -> tridiagonal (default). Applies to
+ * both precision routes and to the complex, batched and singularity-check solves. */
+int elsi_set_elpa_solver(elsi_handle h, int solver);
 int elsi_set_refine_max_iter(elsi_handle h, int iters);    /* 0..8 */
 int elsi_set_stream(elsi_handle h, void *cuda_stream);     /* cudaStream_t */
 /* Reuse the Cholesky factor of the previous call instead of factorising ovlp again

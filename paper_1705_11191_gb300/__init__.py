@@ -83,6 +83,7 @@ def _declare(lib):
         "elsi_batch_dm": ([H, _vp, _pp, _pp, _dp], i),
         "elsi_get_entropy": ([H, _dp], i),
         "elsi_set_sing_check": ([H, i], i),
+        "elsi_set_elpa_solver": ([H, i], i),
         "elsi_set_csc": ([H, i, _vp, _vp, i], i),
         "elsi_ev_real_sparse": ([H, _vp, _vp, _vp, _vp], i),
         "elsi_dm_real_sparse": ([H, _vp, _vp, _vp, _dp], i),
@@ -350,6 +351,10 @@ class Handle:
         w = torch.empty(self._csc_nnz, dtype=torch.float64, device="cuda")
         self._check(self._lib.elsi_get_edm_real_sparse(self._h, _vp(_ptr(w))), "elsi_get_edm_real_sparse")
         return w
+
+    def set_elpa_solver(self, solver: int):
+        """1: one-stage tridiagonalisation, 2: two-stage (default)."""
+        self._check(self._lib.elsi_set_elpa_solver(self._h, int(solver)), "elsi_set_elpa_solver")
 
     def set_sing_check(self, mode: int, tol: float | None = None):
         """Singularity check of S (0 off, 1 check, 2 always transform) and its tolerance."""

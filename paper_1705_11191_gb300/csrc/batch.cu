@@ -171,6 +171,7 @@ int batch_ev(elsi_gb_handle_s *h, int nprob, const int *n_basis, const int *n_st
     s->mu_max_steps = h->mu_max_steps;
     s->precision = h->precision;
     s->band_width = h->band_width;
+    s->elpa_solver = h->elpa_solver;
     s->refine_max_iter = h->refine_max_iter;
     s->stream = h->stream;
     s->reuse_l = false;

@@ -130,6 +130,7 @@ elsi_gb_handle_s *complex_handle(elsi_gb_handle_s *h)
     c->mu_max_steps = h->mu_max_steps;
     c->precision = h->precision;
     c->band_width = h->band_width;
+    c->elpa_solver = h->elpa_solver;
     c->refine_max_iter = h->refine_max_iter;
     c->stream = h->stream;
     c->reuse_l = h->reuse_l;

@@ -251,6 +251,14 @@ int elsi_get_edm_real_sparse(elsi_handle h, double *edm)
     return csc_get_edm(h, edm);
 }
 
+int elsi_set_elpa_solver(elsi_handle h, int solver)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (solver != 1 && solver != 2) return set_error(h, ELSI_ERR_ARG, "elpa_solver %d (1 or 2)", solver);
+    h->elpa_solver = solver;
+    return ELSI_OK;
+}
+
 int elsi_set_sing_check(elsi_handle h, int mode)
 {
     if (check_handle(h)) return ELSI_ERR_STATE;

@@ -124,6 +124,17 @@ template <typename T>
 cudaError_t apply_q1(cudaStream_t st, int n, int b, int k, const T *v1, const T *t1, T *z,
                      int ldz, T *work);
 
+// ---- one-stage tridiagonalisation (Eq. 11 line 1; onestage.cu) ----
+constexpr int kOneStageNb = 32;  // panel width (T factors: kOneStageNb x n in t1)
+size_t onestage_work_elems(int n);  // binary64 scratch elements
+template <typename T>
+cudaError_t onestage_tridiag(cudaStream_t st, int n, T *A, int lda, double *d, double *e, T *v1,
+                             T *t1, double *work);
+// Z <- Q Z; work: 18 kOneStageNb k elements
+template <typename T>
+cudaError_t apply_q_onestage(cudaStream_t st, int n, int k, const T *v1, const T *t1, T *z, int ldz,
+                             T *work);
+
 // ---- occupation, density matrices ----
 // stride 2: consecutive pairs of states are one complex state (see density.cu).
 cudaError_t occupation(cudaStream_t st, int k, const double *eps, double n_el, int scheme,

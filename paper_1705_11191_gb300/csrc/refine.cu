@@ -400,21 +400,29 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
         CKR(copy_matrix<float, double>(st, n, n, rq.ham, n, A, n));
         CKR(symmetrize<float>(st, n, A, n));
     }
+    const bool one_stage = h->elpa_solver == 1;
     CKR(cudaEventRecord(w.ev[STAGE_SY2SB], st));
-    CKR(sy2sb<float>(st, n, b, A, n, V1, T1, WORK, w.work_cap / sizeof(float), w.sync, w.status, sms));
-    CKR(cudaEventRecord(w.ev[STAGE_SB2ST], st));
-    const int ldb = 2 * b + 1;
-    CKR(extract_band<float>(st, n, b, A, n, BAND, ldb));
-    CKR(sb2st<float>(st, n, b, BAND, ldb, w.d, w.e, V2, TAU2, w.status, w.sync, sms));
+    if (one_stage) {
+        // Eq. 11 first form: T = Q^T H~ Q directly
+        CKR(onestage_tridiag<float>(st, n, A, n, w.d, w.e, V1, T1, w.work));
+        CKR(cudaEventRecord(w.ev[STAGE_SB2ST], st));
+    } else {
+        CKR(sy2sb<float>(st, n, b, A, n, V1, T1, WORK, w.work_cap / sizeof(float), w.sync, w.status, sms));
+        CKR(cudaEventRecord(w.ev[STAGE_SB2ST], st));
+        const int ldb = 2 * b + 1;
+        CKR(extract_band<float>(st, n, b, A, n, BAND, ldb));
+        CKR(sb2st<float>(st, n, b, BAND, ldb, w.d, w.e, V2, TAU2, w.status, w.sync, sms));
+    }
     CKR(cudaEventRecord(w.ev[STAGE_TRIDIAG], st));
     // binary32-route eigenvalues: the wanted ones are recomputed by the refinement and the
     // rest are reported at the accuracy of this route, so 1e-10 ||T|| suffices
     CKR(stebz(st, n, w.d, w.e, n, w.w, w.status, 1e-10));
     CKR(stein<float>(st, n, w.d, w.e, n, w.w, X32, n, w.stein, nullptr, w.status));
     CKR(cudaEventRecord(w.ev[STAGE_Q2], st));
-    CKR(apply_q2_tc(st, n, b, V2, TAU2, n, X32, n, w.q2f));
+    if (!one_stage) CKR(apply_q2_tc(st, n, b, V2, TAU2, n, X32, n, w.q2f));
     CKR(cudaEventRecord(w.ev[STAGE_Q1], st));
-    CKR(apply_q1<float>(st, n, b, n, V1, T1, X32, n, WORK));
+    if (one_stage) CKR(apply_q_onestage<float>(st, n, n, V1, T1, X32, n, WORK));
+    else CKR(apply_q1<float>(st, n, b, n, V1, T1, X32, n, WORK));
     CKR(cudaEventRecord(w.ev[STAGE_BACKSUB], st));
     if (!unit) CKR(trsm_left_lower<float>(st, 1, n, n, L, n, INVD, X32, n, WORK));
     CKR(cudaEventRecord(w.ev[STAGE_REFINE], st));

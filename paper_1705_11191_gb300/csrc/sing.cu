@@ -191,6 +191,7 @@ int solve_singular(elsi_gb_handle_s *h, const SolveRequest &rq)
     r->overlap_is_unit = true;
     r->precision = h->precision;
     r->band_width = h->band_width;
+    r->elpa_solver = h->elpa_solver;
     r->refine_max_iter = h->refine_max_iter;
     r->stream = st;
     SolveRequest q;

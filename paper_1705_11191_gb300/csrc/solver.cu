@@ -44,12 +44,14 @@ int ensure_workspace(elsi_gb_handle_s *h, int kz)
     ENSURE(v2, double, nsweep * S * b);
     ENSURE(tau2, double, nsweep * S);
     ENSURE(band, double, (2 * b + 1) * n);
-    ENSURE(t1, double, (size_t)b * n);
+    ENSURE(t1, double, (size_t)(b > kOneStageNb ? b : kOneStageNb) * n);
     ENSURE(invd, double, n * kTriBlock);
     size_t work = n * kTriBlock;
     size_t wsy = sy2sb_work_elems(h->n, b);
     if (wsy > work) work = wsy;
     if ((size_t)18 * b * kz > work) work = (size_t)18 * b * kz;
+    if ((size_t)18 * kOneStageNb * kz > work) work = (size_t)18 * kOneStageNb * kz;
+    if (h->elpa_solver == 1 && onestage_work_elems(h->n) > work) work = onestage_work_elems(h->n);
     ENSURE(work, double, work + 64);
     ENSURE(z, double, n * kz);
     ENSURE(d, double, n + 8);
@@ -134,15 +136,22 @@ static int solve_fp64(elsi_gb_handle_s *h, const SolveRequest &rq)
         CK(copy_matrix<double, double>(st, n, n, rq.ham, n, A, n));
         CK(symmetrize<double>(st, n, A, n));
     }
+    const bool one_stage = h->elpa_solver == 1;
     CK(cudaEventRecord(w.ev[STAGE_SY2SB], st));
-    // ---- Eq. 11 (1): full -> band
-    CK(sy2sb<double>(st, n, b, A, n, w.v1, w.t1, w.work, w.work_cap / sizeof(double), w.sync,
-                     w.status, sms));
-    CK(cudaEventRecord(w.ev[STAGE_SB2ST], st));
-    // ---- Eq. 11 (2): band -> tridiagonal
-    const int ldb = 2 * b + 1;
-    CK(extract_band<double>(st, n, b, A, n, w.band, ldb));
-    CK(sb2st<double>(st, n, b, w.band, ldb, w.d, w.e, w.v2, w.tau2, w.status, w.sync, sms));
+    if (one_stage) {
+        // ---- Eq. 11, first form: T = Q^T H~ Q directly (ELPA 1-stage)
+        CK(onestage_tridiag<double>(st, n, A, n, w.d, w.e, w.v1, w.t1, w.work));
+        CK(cudaEventRecord(w.ev[STAGE_SB2ST], st));
+    } else {
+        // ---- Eq. 11 (1): full -> band
+        CK(sy2sb<double>(st, n, b, A, n, w.v1, w.t1, w.work, w.work_cap / sizeof(double), w.sync,
+                         w.status, sms));
+        CK(cudaEventRecord(w.ev[STAGE_SB2ST], st));
+        // ---- Eq. 11 (2): band -> tridiagonal
+        const int ldb = 2 * b + 1;
+        CK(extract_band<double>(st, n, b, A, n, w.band, ldb));
+        CK(sb2st<double>(st, n, b, w.band, ldb, w.d, w.e, w.v2, w.tau2, w.status, w.sync, sms));
+    }
     CK(cudaEventRecord(w.ev[STAGE_TRIDIAG], st));
     // ---- step (3): eigenvalues (all n for ev, the n_state lowest for dm), k vectors
     const int nval = ev_mode ? n : k;
@@ -150,10 +159,11 @@ static int solve_fp64(elsi_gb_handle_s *h, const SolveRequest &rq)
     CK(stein<double>(st, n, w.d, w.e, k, w.w, w.z, n, w.stein, nullptr, w.status));
     CK(cudaEventRecord(w.ev[STAGE_Q2], st));
     // ---- step (4): Z <- Q2 Z
-    CK(apply_q2<double>(st, n, b, w.v2, w.tau2, k, w.z, n, w.status));
+    if (!one_stage) CK(apply_q2<double>(st, n, b, w.v2, w.tau2, k, w.z, n, w.status));
     CK(cudaEventRecord(w.ev[STAGE_Q1], st));
-    // ---- step (5): Z <- Q1 Z
-    CK(apply_q1<double>(st, n, b, k, w.v1, w.t1, w.z, n, w.work));
+    // ---- step (5): Z <- Q1 Z (one-stage: Z <- Q Z)
+    if (one_stage) CK(apply_q_onestage<double>(st, n, k, w.v1, w.t1, w.z, n, w.work));
+    else CK(apply_q1<double>(st, n, b, k, w.v1, w.t1, w.z, n, w.work));
     CK(cudaEventRecord(w.ev[STAGE_BACKSUB], st));
     // ---- Eq. 9: c = L^{-T} c~
     if (!unit) CK(trsm_left_lower<double>(st, 1, n, k, w.l, n, w.invd, w.z, n, w.work));

@@ -78,6 +78,7 @@ struct elsi_gb_handle_s {
     int mu_max_steps = 200;
     int precision = ELSI_PREC_FP64;
     int band_width = 64;
+    int elpa_solver = 2;  // 1: one-stage tridiagonalisation, 2: two-stage (sec. 4.5 elpa_solver)
     int refine_max_iter = 4;
     bool reuse_l = false;
     cudaStream_t stream = nullptr;
