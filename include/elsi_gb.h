@@ -278,6 +278,12 @@ int elsi_dm_batched_complex(elsi_handle h, int nprob, const int *n_basis, const 
                             double *const *den_mat, double *const *edm, double *energy,
                             double *mu);
 
+/* Number of problems of a batched call solved at the same time, each by its own solver
+ * instance on its own stream and host thread (0, the default: 4 for problems up to
+ * n = 4096 in the real form, 2 up to 8192, else 1; at most 16). Each instance keeps its
+ * own workspace for the largest problem it solves. */
+int elsi_set_batch_streams(elsi_handle h, int streams);
+
 /* Phase 1: eigenpairs of every problem, kept in the handle. eval (device, may be NULL)
  * receives the n_state[i] lowest eigenvalues of each problem, concatenated in problem
  * order (sum_i n_state[i] doubles). */

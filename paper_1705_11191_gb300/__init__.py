@@ -84,6 +84,7 @@ def _declare(lib):
         "elsi_get_entropy": ([H, _dp], i),
         "elsi_set_sing_check": ([H, i], i),
         "elsi_set_elpa_solver": ([H, i], i),
+        "elsi_set_batch_streams": ([H, i], i),
         "elsi_set_csc": ([H, i, _vp, _vp, i], i),
         "elsi_ev_real_sparse": ([H, _vp, _vp, _vp, _vp], i),
         "elsi_dm_real_sparse": ([H, _vp, _vp, _vp, _dp], i),
@@ -351,6 +352,10 @@ class Handle:
         w = torch.empty(self._csc_nnz, dtype=torch.float64, device="cuda")
         self._check(self._lib.elsi_get_edm_real_sparse(self._h, _vp(_ptr(w))), "elsi_get_edm_real_sparse")
         return w
+
+    def set_batch_streams(self, streams: int):
+        """Concurrent solves in batched calls (0: chosen by problem size)."""
+        self._check(self._lib.elsi_set_batch_streams(self._h, int(streams)), "elsi_set_batch_streams")
 
     def set_elpa_solver(self, solver: int):
         """1: one-stage tridiagonalisation, 2: two-stage (default)."""

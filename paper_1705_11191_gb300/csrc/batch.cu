@@ -11,7 +11,10 @@
 //      weights (occupation_weighted), or one per problem;
 //   3. batch_dm: P_i = C_i diag(f_i) C_i^H and W_i = C_i diag(f_i eps_i) C_i^H, and the
 //      band energy sum_l f_il eps_il of each problem.
+#include <mutex>
 #include <new>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -27,8 +30,14 @@ struct BatchItem {
     size_t off_lvl = 0;      // state eigenvalues / occupations: k entries
 };
 
+struct BatchWorker {
+    elsi_gb_handle_s *sub = nullptr;  // solver instance of this worker
+    cudaStream_t stream = nullptr;    // its stream (created here)
+};
+
 struct BatchState {
-    elsi_gb_handle_s *sub = nullptr;  // solver instance the problems run in
+    elsi_gb_handle_s *sub = nullptr;  // solver instance the problems run in (worker 0)
+    std::vector<BatchWorker> workers; // workers 1 .. W-1 (own handle, stream, host thread)
     std::vector<BatchItem> items;
     bool cplx = false;
     size_t total_lvl = 0;
@@ -163,54 +172,125 @@ int batch_ev(elsi_gb_handle_s *h, int nprob, const int *n_basis, const int *n_st
         BCK(cudaMemcpyAsync(b.offs, off.data(), sizeof(int) * (nprob + 1), cudaMemcpyHostToDevice, h->stream));
         BCK(cudaStreamSynchronize(h->stream));
     }
-    elsi_gb_handle_s *s = b.sub;
-    s->overlap_is_unit = h->overlap_is_unit;
-    s->scheme = h->scheme;
-    s->kt = h->kt;
-    s->occ_accuracy = h->occ_accuracy;
-    s->mu_max_steps = h->mu_max_steps;
-    s->precision = h->precision;
-    s->band_width = h->band_width;
-    s->elpa_solver = h->elpa_solver;
-    s->refine_max_iter = h->refine_max_iter;
-    s->stream = h->stream;
-    s->reuse_l = false;
-    s->occ_stride = cplx ? 2 : 1;
+    // workers: W solver instances, each with its own stream and host thread (a solve is
+    // synchronous on its host thread); problems i = t, t + W, ... go to worker t
+    size_t nmax = 0;
+    for (auto &it : b.items) nmax = (size_t)(cplx ? 2 : 1) * it.n > nmax ? (size_t)(cplx ? 2 : 1) * it.n : nmax;
+    int W = h->batch_workers;
+    if (W <= 0) W = nmax <= 4096 ? 4 : (nmax <= 8192 ? 2 : 1);
+    if (W > nprob) W = nprob;
+    while ((int)b.workers.size() < W - 1) {
+        BatchWorker wk;
+        wk.sub = new (std::nothrow) elsi_gb_handle_s();
+        if (!wk.sub) return set_error(h, ELSI_ERR_NOMEM, "batch worker");
+        wk.sub->magic = kHandleMagic;
+        if (cudaStreamCreateWithFlags(&wk.stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete wk.sub;
+            return set_error(h, ELSI_ERR_CUDA, "batch worker stream");
+        }
+        b.workers.push_back(wk);
+    }
+    auto configure = [&](elsi_gb_handle_s *s, cudaStream_t wst) {
+        s->overlap_is_unit = h->overlap_is_unit;
+        s->scheme = h->scheme;
+        s->kt = h->kt;
+        s->occ_accuracy = h->occ_accuracy;
+        s->mu_max_steps = h->mu_max_steps;
+        s->precision = h->precision;
+        s->band_width = h->band_width;
+        s->elpa_solver = h->elpa_solver;
+        s->refine_max_iter = h->refine_max_iter;
+        s->stream = wst;
+        s->reuse_l = false;
+        s->occ_stride = cplx ? 2 : 1;
+    };
+    cudaStream_t st = h->stream;
+    BCK(cudaStreamSynchronize(st));  // inputs produced on the caller's stream are ready
+    int dev = 0;
+    cudaGetDevice(&dev);
+    struct Result {
+        int rc = ELSI_OK;
+        std::string msg;
+        float stage_ms[kNumStages] = {};
+        int refine_min = 1 << 30;
+        double orth_max = 0.0;
+    };
+    std::vector<Result> res(W);
+    auto work = [&](int t) {
+        cudaSetDevice(dev);
+        elsi_gb_handle_s *s = (t == 0) ? b.sub : b.workers[t - 1].sub;
+        cudaStream_t wst = (t == 0) ? st : b.workers[t - 1].stream;
+        configure(s, wst);
+        Result &r = res[t];
+        for (int i = t; i < nprob; i += W) {
+            const BatchItem &it = b.items[i];
+            const size_t N = cplx ? 2 * (size_t)it.n : it.n;
+            s->n = (int)N;
+            s->n_state = cplx ? 2 * it.k : it.k;
+            s->n_electron = 0.0;
+            s->have_l = false;
+            SolveRequest rq;
+            rq.ham = ham[i];
+            rq.ovlp = h->overlap_is_unit ? nullptr : ovlp[i];
+            cudaError_t ce = cudaSuccess;
+            if (cplx) {
+                Workspace &sw = s->wk;
+                if (!ensure_buf((void **)&sw.host_h, &sw.host_h_cap, sizeof(double) * N * N) ||
+                    (rq.ovlp && !ensure_buf((void **)&sw.host_s, &sw.host_s_cap, sizeof(double) * N * N))) {
+                    r.rc = ELSI_ERR_NOMEM;
+                    r.msg = "batch: real-form buffers";
+                    return;
+                }
+                ce = embed_hermitian(wst, it.n, ham[i], sw.host_h);
+                if (ce == cudaSuccess && rq.ovlp) ce = embed_hermitian(wst, it.n, ovlp[i], sw.host_s);
+                rq.ham = sw.host_h;
+                rq.ovlp = rq.ovlp ? sw.host_s : nullptr;
+            }
+            if (ce != cudaSuccess) {
+                r.rc = ELSI_ERR_CUDA;
+                r.msg = cudaGetErrorString(ce);
+                return;
+            }
+            rq.eval = b.vals + it.off_val;
+            rq.evec = b.vecs + it.off_vec;
+            const int rc2 = run_solve(s, rq);
+            if (rc2) {
+                r.rc = rc2;
+                r.msg = "batch problem " + std::to_string(i) + ": " + s->last_error;
+                return;
+            }
+            ce = cplx ? pair_evals(wst, it.k, b.vals + it.off_val, b.lvl + it.off_lvl)
+                      : cudaMemcpyAsync(b.lvl + it.off_lvl, b.vals + it.off_val, sizeof(double) * it.k,
+                                        cudaMemcpyDeviceToDevice, wst);
+            if (ce != cudaSuccess) {
+                r.rc = ELSI_ERR_CUDA;
+                r.msg = cudaGetErrorString(ce);
+                return;
+            }
+            for (int q = 0; q < kNumStages; ++q) r.stage_ms[q] += s->stage_ms[q];
+            if (s->refine_iters < r.refine_min) r.refine_min = s->refine_iters;
+            if (s->orth_err > r.orth_max) r.orth_max = s->orth_err;
+        }
+        const cudaError_t ce = cudaStreamSynchronize(wst);
+        if (ce != cudaSuccess && r.rc == ELSI_OK) {
+            r.rc = ELSI_ERR_CUDA;
+            r.msg = cudaGetErrorString(ce);
+        }
+    };
+    {
+        std::vector<std::thread> threads;
+        for (int t = 1; t < W; ++t) threads.emplace_back(work, t);
+        work(0);
+        for (auto &th : threads) th.join();
+    }
     float stage_ms[kNumStages] = {};
     int refine_min = 1 << 30;
     double orth_max = 0.0;
-    cudaStream_t st = h->stream;
-    for (int i = 0; i < nprob; ++i) {
-        const BatchItem &it = b.items[i];
-        const size_t N = cplx ? 2 * (size_t)it.n : it.n;
-        s->n = (int)N;
-        s->n_state = cplx ? 2 * it.k : it.k;
-        s->n_electron = 0.0;
-        s->have_l = false;
-        SolveRequest rq;
-        rq.ham = ham[i];
-        rq.ovlp = h->overlap_is_unit ? nullptr : ovlp[i];
-        if (cplx) {
-            Workspace &sw = s->wk;
-            if (!ensure_buf((void **)&sw.host_h, &sw.host_h_cap, sizeof(double) * N * N) ||
-                (rq.ovlp && !ensure_buf((void **)&sw.host_s, &sw.host_s_cap, sizeof(double) * N * N)))
-                return set_error(h, ELSI_ERR_NOMEM, "batch: real-form buffers");
-            BCK(embed_hermitian(st, it.n, ham[i], sw.host_h));
-            if (rq.ovlp) BCK(embed_hermitian(st, it.n, ovlp[i], sw.host_s));
-            rq.ham = sw.host_h;
-            rq.ovlp = rq.ovlp ? sw.host_s : nullptr;
-        }
-        rq.eval = b.vals + it.off_val;
-        rq.evec = b.vecs + it.off_vec;
-        rc = run_solve(s, rq);
-        if (rc) return set_error(h, rc, "batch problem %d: %s", i, s->last_error.c_str());
-        if (cplx) BCK(pair_evals(st, it.k, b.vals + it.off_val, b.lvl + it.off_lvl));
-        else
-            BCK(cudaMemcpyAsync(b.lvl + it.off_lvl, b.vals + it.off_val, sizeof(double) * it.k,
-                                cudaMemcpyDeviceToDevice, st));
-        for (int q = 0; q < kNumStages; ++q) stage_ms[q] += s->stage_ms[q];
-        if (s->refine_iters < refine_min) refine_min = s->refine_iters;
-        if (s->orth_err > orth_max) orth_max = s->orth_err;
+    for (int t = 0; t < W; ++t) {
+        if (res[t].rc) return set_error(h, res[t].rc, "%s", res[t].msg.c_str());
+        for (int q = 0; q < kNumStages; ++q) stage_ms[q] += res[t].stage_ms[q];
+        refine_min = res[t].refine_min < refine_min ? res[t].refine_min : refine_min;
+        orth_max = res[t].orth_max > orth_max ? res[t].orth_max : orth_max;
     }
     if (eval) BCK(cudaMemcpyAsync(eval, b.lvl, sizeof(double) * nlvl, cudaMemcpyDeviceToDevice, st));
     BCK(cudaStreamSynchronize(st));
@@ -334,6 +414,14 @@ void free_batch(elsi_gb_handle_s *h)
         free_complex(b.sub);
         free_workspace(b.sub);
         delete b.sub;
+    }
+    for (auto &wk : b.workers) {
+        if (wk.sub) {
+            free_complex(wk.sub);
+            free_workspace(wk.sub);
+            delete wk.sub;
+        }
+        if (wk.stream) cudaStreamDestroy(wk.stream);
     }
     delete h->batch;
     h->batch = nullptr;

@@ -251,6 +251,14 @@ int elsi_get_edm_real_sparse(elsi_handle h, double *edm)
     return csc_get_edm(h, edm);
 }
 
+int elsi_set_batch_streams(elsi_handle h, int streams)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (streams < 0 || streams > 16) return set_error(h, ELSI_ERR_ARG, "batch streams %d (0..16)", streams);
+    h->batch_workers = streams;
+    return ELSI_OK;
+}
+
 int elsi_set_elpa_solver(elsi_handle h, int solver)
 {
     if (check_handle(h)) return ELSI_ERR_STATE;

@@ -99,6 +99,7 @@ struct elsi_gb_handle_s {
     bool have_cedm = false;
     // several independent problems (k-points / spin channels): batch.cu
     egb::BatchState *batch = nullptr;
+    int batch_workers = 0;  // concurrent solves of a batch (0: by problem size)
     // singularity check of the overlap (sec. 4.4): sing.cu. sing_mode 0 = off, 1 = check,
     // 2 = always transform by the eigendecomposition of S
     int sing_mode = 0;

@@ -188,3 +188,24 @@ def test_batch_errors():
         P, W, en, mu = hd.dm_batched([dev(p.h)], [dev(p.s)], [20], 10.0, weights=[1.0])
         ref = oracle.solve(p.h, p.s, 20, 10.0)
         assert rel(P[0].cpu().numpy(), ref["P"]) <= 1e-9
+
+
+def test_concurrent_workers_match_one_stream():
+    """Problems solved by several concurrent solver instances (own streams and host
+    threads) give the same result as one after another."""
+    probs = _real_problems([64, 96, 80, 128, 72, 100, 90, 110], 120)
+    ks = [p.n // 2 for p in probs]
+    wts = [0.125] * 8
+    n_el = sum(w * p.n / 4 for w, p in zip(wts, probs))
+    hs, ss = [dev(p.h) for p in probs], [dev(p.s) for p in probs]
+    out = {}
+    for streams in (1, 4):
+        with _handle(scheme=egb.OCC_FERMI, kt=0.01) as hd:
+            hd.set_batch_streams(streams)
+            out[streams] = hd.dm_batched(hs, ss, ks, n_el, weights=wts)
+    assert abs(out[1][3] - out[4][3]) <= 1e-13
+    for a, b in zip(out[1][0], out[4][0]):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) <= 1e-13
+    ref, ref_mu = oracle.solve_batched([(p.h, p.s, k) for p, k in zip(probs, ks)], n_el,
+                                       weights=wts, scheme=oracle.SCHEME_FERMI, kt=0.01)
+    _check(out[4], ref, out[4][3], ref_mu)
