@@ -120,6 +120,13 @@ cudaError_t apply_q2(cudaStream_t st, int n, int b, const T *v2, const T *tau2, 
 size_t q2_tfactor_elems(int n, int b);
 cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const float *tau2, int k,
                         float *z, int ldz, float *tfac);
+// Z <- Q1 Z in groups of kQ1Group panels; work: q1_work_elems(b, k) elements.
+constexpr int kQ1Group = 4;
+inline size_t q1_work_elems(int b, int k)
+{
+    const size_t g = (size_t)kQ1Group * b;
+    return g * g + 2 * g * b + 4 * g * (size_t)k + 64;
+}
 template <typename T>
 cudaError_t apply_q1(cudaStream_t st, int n, int b, int k, const T *v1, const T *t1, T *z,
                      int ldz, T *work);

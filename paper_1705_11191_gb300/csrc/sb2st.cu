@@ -506,6 +506,11 @@ template cudaError_t apply_q2<float>(cudaStream_t, int, int, const float *, cons
 
 // ------------------------------------------------------------------ Q1 back-transform
 // Z <- Q1 Z, Q1 = Q_0 Q_1 ... Q_{P-1}, Q_p = I - V_p T_p V_p^T: panels descending.
+// Z <- Q1 Z, Q1 = Q_0 Q_1 ... Q_{P-1} (panels of the full-to-band reduction, each
+// Q_p = I - V_p T_p V_p^T). Groups of up to kQ1Group consecutive panels are applied as one
+// compact-WY block Q_g = I - V T V^T, V = [V_p ... V_q] (explicit, zero above each panel's
+// first row), T merged pairwise as [[T_a, -T_a (V_a^T V_b) T_b], [0, T_b]]: the passes
+// over Z fall by the group size and the products have K = group width.
 template <typename T>
 cudaError_t apply_q1(cudaStream_t st, int n, int b, int k, const T *v1, const T *t1, T *z,
                      int ldz, T *work)
@@ -513,20 +518,42 @@ cudaError_t apply_q1(cudaStream_t st, int n, int b, int k, const T *v1, const T 
     cudaError_t e;
     int npan = 0;
     for (int c0 = 0; c0 + b <= n - 2; c0 += b) ++npan;
-    for (int p = npan - 1; p >= 0; --p) {
-        const int c0 = p * b, r0 = c0 + b, m = n - r0;
-        const T *V = v1 + r0 + (size_t)c0 * n;
-        const T *Tm = t1 + (size_t)c0 * b;
-        T *Y = work;                    // b x k
-        T *Y2 = work + (size_t)b * k;   // b x k
+    const int gw_max = kQ1Group * b;
+    T *Tg = work;                                  // gw_max x gw_max (ld gw_max)
+    T *M1 = Tg + (size_t)gw_max * gw_max;          // gw_max x b
+    T *M2 = M1 + (size_t)gw_max * b;               // gw_max x b
+    T *Y = M2 + (size_t)gw_max * b;                // gw_max x k
+    T *Y2 = Y + (size_t)gw_max * k;                // gw_max x k
+    T *part = Y2 + (size_t)gw_max * k;             // split-K partials (what is left)
+    const size_t part_elems = (size_t)2 * gw_max * k;
+    for (int phi = npan - 1; phi >= 0; phi -= kQ1Group) {
+        const int plo = phi - kQ1Group + 1 < 0 ? 0 : phi - kQ1Group + 1;
+        const int c0 = plo * b, r0 = c0 + b, m = n - r0;
+        const int gw = (phi - plo + 1) * b;
+        const T *V = v1 + r0 + (size_t)c0 * n;  // m x gw
+        // T of the group: start from the first panel's T, merge the others in order
+        if ((e = copy_matrix<T, T>(st, b, b, t1 + (size_t)c0 * b, b, Tg, gw_max)) != cudaSuccess) return e;
+        for (int p = plo + 1; p <= phi; ++p) {
+            const int wa = (p - plo) * b;             // width merged so far
+            const T *Vb = v1 + r0 + (size_t)(p * b) * n;
+            const T *Tb = t1 + (size_t)(p * b) * b;
+            // M1 = V_a^T V_b (wa x b), M2 = M1 T_b, T12 = -T_a M2
+            if ((e = gemm<T>(st, 1, 0, wa, b, m, T(1), V, n, Vb, n, T(0), M1, gw_max)) != cudaSuccess) return e;
+            if ((e = gemm<T>(st, 0, 0, wa, b, b, T(1), M1, gw_max, Tb, b, T(0), M2, gw_max)) != cudaSuccess) return e;
+            if ((e = gemm<T>(st, 0, 0, wa, b, wa, T(-1), Tg, gw_max, M2, gw_max, T(0), Tg + (size_t)wa * gw_max,
+                             gw_max)) != cudaSuccess) return e;
+            // T22 = T_b, T21 = 0
+            if ((e = copy_matrix<T, T>(st, b, b, Tb, b, Tg + wa + (size_t)wa * gw_max, gw_max)) != cudaSuccess) return e;
+            if ((e = cudaMemset2DAsync(Tg + wa, sizeof(T) * gw_max, 0, sizeof(T) * b, wa, st)) != cudaSuccess) return e;
+        }
         T *Zr = z + r0;
-        if ((e = gemm_splitk<T>(st, 1, 0, b, k, m, T(1), V, n, Zr, ldz, Y, b, Y2 + (size_t)b * k,
-                                (size_t)16 * b * k)) != cudaSuccess) return e;
-        if ((e = gemm<T>(st, 0, 0, b, k, b, T(1), Tm, b, Y, b, T(0), Y2, b)) != cudaSuccess) return e;
-        if ((e = gemm<T>(st, 0, 0, m, k, b, T(-1), V, n, Y2, b, T(1), Zr, ldz)) != cudaSuccess) return e;
+        if ((e = gemm_splitk<T>(st, 1, 0, gw, k, m, T(1), V, n, Zr, ldz, Y, gw, part, part_elems)) != cudaSuccess) return e;
+        if ((e = gemm<T>(st, 0, 0, gw, k, gw, T(1), Tg, gw_max, Y, gw, T(0), Y2, gw)) != cudaSuccess) return e;
+        if ((e = gemm<T>(st, 0, 0, m, k, gw, T(-1), V, n, Y2, gw, T(1), Zr, ldz)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
+
 template cudaError_t apply_q1<double>(cudaStream_t, int, int, int, const double *, const double *,
                                       double *, int, double *);
 template cudaError_t apply_q1<float>(cudaStream_t, int, int, int, const float *, const float *,

@@ -51,6 +51,7 @@ int ensure_workspace(elsi_gb_handle_s *h, int kz)
     if (wsy > work) work = wsy;
     if ((size_t)18 * b * kz > work) work = (size_t)18 * b * kz;
     if ((size_t)18 * kOneStageNb * kz > work) work = (size_t)18 * kOneStageNb * kz;
+    if (q1_work_elems(b, kz) > work) work = q1_work_elems(b, kz);
     if (h->elpa_solver == 1 && onestage_work_elems(h->n) > work) work = onestage_work_elems(h->n);
     ENSURE(work, double, work + 64);
     ENSURE(z, double, n * kz);

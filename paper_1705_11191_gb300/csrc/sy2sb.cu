@@ -210,6 +210,9 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
 
     int dev = 0;
     cudaGetDevice(&dev);
+    // V1 explicit and zero outside each panel's reflectors (the back-transformation merges
+    // consecutive panels into one block)
+    if ((e = cudaMemsetAsync(v1, 0, sizeof(T) * (size_t)n * n, st)) != cudaSuccess) return e;
     for (int c0 = 0; c0 + b <= n - 2; c0 += b) {
         const int r0 = c0 + b;
         const int m = n - r0;
