@@ -11,8 +11,8 @@
 // current window of its 128 columns of Z in a shared-memory ring and performs, per group,
 //     Y = V^T Z_w,  Y = T^T Y,  Z_w -= V Y
 // with mma.sync m16n8k8 TF32 products in three-pass split precision
-// (x = x_hi + x_lo, x_hi = tf32(x); A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi), which keeps
-// binary32 accuracy.
+// (x = x_hi + x_lo, x_hi = x truncated to tf32; A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi),
+// about binary32 accuracy.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -31,17 +31,14 @@ constexpr int kWyGroupWords = kWyM * kWyRows + kWyM * kWyM;
 
 __device__ __forceinline__ int wy_steps(int n, int b, int j) { return (n - 2 - j) / b + 1; }
 
-__device__ __forceinline__ unsigned to_tf32(float x)
-{
-    unsigned r;
-    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-    return r;
-}
 
+// x = hi + lo with hi = x truncated to TF32 (one bit mask) and lo = x - hi (exact); the
+// tensor core reads lo truncated to TF32 as well, which leaves an error below
+// 2^-20 |x|, ample for the binary32 route that the refinement corrects.
 __device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo)
 {
-    hi = to_tf32(x);
-    lo = to_tf32(x - __uint_as_float(hi));
+    hi = __float_as_uint(x) & 0xFFFFE000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
 // ---------------------------------------------------------------- T factors
