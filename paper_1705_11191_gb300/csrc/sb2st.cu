@@ -134,12 +134,6 @@ __device__ void two_sided(int L, T *D, int ldd, const T *v, T tau, T *p, T *red)
 template <typename T>
 __device__ __forceinline__ T ldg_l2(const T *p) { return __ldcg(p); }
 
-template <typename T>
-__device__ __forceinline__ T band_get(const T *band, int ldb, int r, int c)
-{
-    return (r >= c) ? ldg_l2(band + (size_t)(r - c) + (size_t)c * ldb)
-                    : ldg_l2(band + (size_t)(c - r) + (size_t)r * ldb);
-}
 
 // One (sweep j, step t) task; all threads of the CTA take part. The b x b tiles use the
 // leading dimension b + 8, which makes the four-lanes-per-row dot products
@@ -163,9 +157,12 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
         const int L = min(b, n - 1 - j);
         const int r0 = j + 1;
         for (int i = tid; i < b; i += nt) vnew[i] = (i < L) ? ldg_l2(band + (size_t)(1 + i) + (size_t)j * ldb) : T(0);
-        // D = A[j+1 .. j+L]^2
+        // D = A[j+1 .. j+L]^2: lower triangle from the band, upper by symmetry
         if (ti < L)
-            for (int c = tc; c < L; c += 4) D[ti + c * ld] = band_get(band, ldb, r0 + ti, r0 + c);
+            for (int c = tc; c <= ti; c += 4) D[ti + c * ld] = ldg_l2(band + (size_t)(ti - c) + (size_t)(r0 + c) * ldb);
+        __syncthreads();
+        if (ti < L)
+            for (int c = ti + 1 + tc; c < L; c += 4) D[ti + c * ld] = D[c + ti * ld];
         __syncthreads();
         T beta;
         T tau = house_smem<T>(L, vnew, red, &beta);
@@ -188,9 +185,13 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     // X = A[r .. r+L-1, cb .. cb+b-1]  (all strictly below the diagonal, distance 1..2b-1)
     if (ti < L)
         for (int c = tc; c < b; c += 4) X[ti + c * ld] = ldg_l2(band + (size_t)(r + ti - (cb + c)) + (size_t)(cb + c) * ldb);
-    // D = A[r .. r+L-1]^2 (read now: the task's window is not touched by anyone else)
+    // D = A[r .. r+L-1]^2 (read now: the task's window is not touched by anyone else);
+    // lower triangle from the band, upper by symmetry
     if (ti < L)
-        for (int c = tc; c < L; c += 4) D[ti + c * ld] = band_get(band, ldb, r + ti, r + c);
+        for (int c = tc; c <= ti; c += 4) D[ti + c * ld] = ldg_l2(band + (size_t)(ti - c) + (size_t)(r + c) * ldb);
+    __syncthreads();
+    if (ti < L)
+        for (int c = ti + 1 + tc; c < L; c += 4) D[ti + c * ld] = D[c + ti * ld];
     __syncthreads();
     // X <- X H_prev : y = X v, X -= tau y v^T
     if (taup != T(0)) {
