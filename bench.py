@@ -240,8 +240,10 @@ def main():
            "tflops_algorithmic": algorithmic_flops(n, k) / (ms * 1e-3) / 1e12,
            "clocks": cs.summary()}
 
-    # roofline of the dominant stage
-    dom = max(stages, key=stages.get)
+    # roofline of the dominant kernel: in the binary32 route the largest single kernel is
+    # the Q2 back-transformation (one launch per solve; the full-to-band stage is longer but
+    # is hundreds of panel-factorisation and GEMM launches); else the largest stage
+    dom = "back_q2" if prec == egb.PREC_FP32_REFINE else max(stages, key=stages.get)
     out["roofline"] = roofline_for(dom, stages[dom], n, k, prec, out["clocks"],
                                    refine_iters=max(iters, 0))
 

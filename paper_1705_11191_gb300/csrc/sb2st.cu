@@ -519,7 +519,10 @@ cudaError_t apply_q1(cudaStream_t st, int n, int b, int k, const T *v1, const T 
     cudaError_t e;
     int npan = 0;
     for (int c0 = 0; c0 + b <= n - 2; c0 += b) ++npan;
-    const int gw_max = kQ1Group * b;
+    // groups of kQ1Group panels on the tensor-core binary32 path; one panel at a time with
+    // the SIMT binary64 GEMM (its split-K products lose parallelism with wide blocks)
+    const int group = sizeof(T) == 4 ? kQ1Group : 1;
+    const int gw_max = group * b;
     T *Tg = work;                                  // gw_max x gw_max (ld gw_max)
     T *M1 = Tg + (size_t)gw_max * gw_max;          // gw_max x b
     T *M2 = M1 + (size_t)gw_max * b;               // gw_max x b
@@ -527,8 +530,8 @@ cudaError_t apply_q1(cudaStream_t st, int n, int b, int k, const T *v1, const T 
     T *Y2 = Y + (size_t)gw_max * k;                // gw_max x k
     T *part = Y2 + (size_t)gw_max * k;             // split-K partials (what is left)
     const size_t part_elems = (size_t)2 * gw_max * k;
-    for (int phi = npan - 1; phi >= 0; phi -= kQ1Group) {
-        const int plo = phi - kQ1Group + 1 < 0 ? 0 : phi - kQ1Group + 1;
+    for (int phi = npan - 1; phi >= 0; phi -= group) {
+        const int plo = phi - group + 1 < 0 ? 0 : phi - group + 1;
         const int c0 = plo * b, r0 = c0 + b, m = n - r0;
         const int gw = (phi - plo + 1) * b;
         const T *V = v1 + r0 + (size_t)c0 * n;  // m x gw
