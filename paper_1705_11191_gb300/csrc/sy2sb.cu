@@ -87,20 +87,30 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             // sigma2 by warp 0; d_c by 64 column lanes x 4 row groups of CTAs
             if (tid < 32) {
                 double v = 0.0;
-                for (int q = tid; q < G; q += 32) v += ((volatile double *)part)[q];
+                for (int q = tid; q < G; q += 32) v += __ldcg(part + q);
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (tid == 0) red[0] = v;
             }
+            // L2-coherent loads (written by other CTAs before the barrier), all issued
+            // before they are summed
             double dv = 0.0;
-            if (tc > j && tc < bw)
-                for (int q = tr; q < G; q += 4) dv += ((volatile double *)dpart)[(size_t)q * 64 + tc];
+            if (tc > j && tc < bw) {
+                double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                int q = tr;
+                for (; q + 12 < G; q += 16) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[u] += __ldcg(dpart + (size_t)(q + 4 * u) * 64 + tc);
+                }
+                for (; q < G; q += 4) acc[0] += __ldcg(dpart + (size_t)q * 64 + tc);
+                dv = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+            }
             colpart[tr][tc] = dv;
             __syncthreads();
             if (tid < bw) wsum[tid] = colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
             __syncthreads();
         }
         const double sigma2 = red[0];
-        const double alpha = ((volatile double *)prow)[j];
+        const double alpha = __ldcg(prow + j);
         double beta, tau, scl;
         if (sigma2 == 0.0) { beta = alpha; tau = 0.0; scl = 0.0; }
         else {
@@ -110,7 +120,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             scl = 1.0 / (alpha - beta);
         }
         // w_c = P[j][c] + scl d_c; stored pre-multiplied by tau
-        if (tid > j && tid < bw) wsum[tid] = tau * (((volatile double *)prow)[tid] + scl * wsum[tid]);
+        if (tid > j && tid < bw) wsum[tid] = tau * (__ldcg(prow + tid) + scl * wsum[tid]);
         __syncthreads();
         const T sclT = (T)scl;
         for (int i = tid; i < nrow; i += blockDim.x)

@@ -90,9 +90,9 @@ __device__ int sturm_count32(int n, const double *__restrict__ d, const double *
 // Bisection for eigenvalue index idx = blockIdx.x * (blockDim.x / LANES) + group, with
 // LANES threads per eigenvalue evaluating LANES interior points of the current interval
 // (multisection: the interval shrinks by LANES + 1 per step).
-// Phase 1 (bracket32 != 0): binary32 counts down to a width of 2e-6 ||T|| (a binary32
+// Phase 1 (bracket32 != 0): binary32 counts down to a width of 1e-6 ||T|| (a binary32
 // Sturm count is exact for a matrix within a few binary32 roundings of T, so its
-// eigenvalues move by far less), then the bracket is widened by 4e-6 ||T|| and checked
+// eigenvalues move by far less), then the bracket is widened by 2e-6 ||T|| and checked
 // with binary64 counts (falling back to the Gershgorin interval if the check fails). Phase 2: binary64 counts down to
 // max(tol_rel * ||T||, 2 eps max|lo|,|hi|).
 template <int LANES>
@@ -109,7 +109,7 @@ __global__ void bisect_kernel(int n, const double *d, const double *e, int count
     if (bracket32 && active) {
         float flo = (float)gl, fhi = (float)gu;
         const float fpiv = fmaxf(1e-30f, (float)pivmin);
-        for (int it = 0; it < 64 && (double)(fhi - flo) > 2e-6 * tn; ++it) {
+        for (int it = 0; it < 64 && (double)(fhi - flo) > 1e-6 * tn; ++it) {
             float sig = flo + (fhi - flo) * (float)(lane + 1) / (float)(LANES + 1);
             int c = sturm_count32(n, d, e, sig, fpiv);
             unsigned ok = __ballot_sync(gmask, c <= idx) & gmask;
@@ -119,8 +119,8 @@ __global__ void bisect_kernel(int n, const double *d, const double *e, int count
             if (pcount > 0) flo = nlo;
             if (pcount < LANES) fhi = nhi;
         }
-        lo = (double)flo - 4e-6 * tn;
-        hi = (double)fhi + 4e-6 * tn;
+        lo = (double)flo - 2e-6 * tn;
+        hi = (double)fhi + 2e-6 * tn;
         if (lo < gl) lo = gl;
         if (hi > gu) hi = gu;
         // verify the bracket in binary64: count(lo) <= idx < count(hi)
