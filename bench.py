@@ -53,9 +53,9 @@ def dist_env():
 def workload(n: int):
     import ksinputs
     if n == 16384:
-        p = ksinputs.config(2)
+        p = ksinputs.workload("cluster3d-n16384")
     elif n == 8192:
-        p = ksinputs.config(1)
+        p = ksinputs.workload("cluster3d-n8192")
     else:
         p = ksinputs.cluster_problem(n, seed=2)
     return p
@@ -231,7 +231,7 @@ def main():
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if prec == egb.PREC_FP32_REFINE else "f64", "data": "synthetic",
-           "config": {"workload": f"3D-cluster KS problem n={n} (config 2), N_el={int(p.n_electron)}, "
+           "config": {"workload": f"3D-cluster KS problem n={n}, N_el={int(p.n_electron)}, "
                                   f"n_state={k}, integer occupation, lambda_min(S)={p.lambda_min_s:.3g}",
                       "precision": args.precision, "parallelism": f"replicas x{world}",
                       "l2": "inputs (2 x 2.1 GB) larger than L2; no flush"},

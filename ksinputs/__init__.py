@@ -28,8 +28,8 @@ import math
 
 import numpy as np
 
-__all__ = ["Problem", "chain_positions", "cluster_positions", "build", "config",
-           "basis_atoms", "CONFIGS"]
+__all__ = ["Problem", "chain_positions", "cluster_positions", "build", "cluster_problem", "chain_problem", "kpoint_problem",
+           "basis_atoms", "WORKLOADS", "workload"]
 
 
 @dataclasses.dataclass
@@ -134,14 +134,14 @@ def _mirror_upper(a: np.ndarray, block: int = 2048) -> None:
                 a[c0:c1, r0:r1] = blk.T
 
 
-# (name, geometry, n, per_atom, n_electron, n_state, seed)
-CONFIGS = {
-    0: dict(name="chain-n512", geometry="chain", n=512, per_atom=8, n_atoms=64,
-            n_electron=256.0, n_state=512, seed=0),
-    1: dict(name="cluster3d-n8192", geometry="cluster", n=8192, per_atom=15, n_atoms=547,
-            n_electron=2048.0, n_state=1024, seed=1),
-    2: dict(name="cluster3d-n16384", geometry="cluster", n=16384, per_atom=15,
-            n_atoms=1093, n_electron=4096.0, n_state=2048, seed=2),
+# The three real workloads by name: geometry, size, electrons, states, seed.
+WORKLOADS = {
+    "chain-n512": dict(geometry="chain", n=512, per_atom=8, n_atoms=64,
+                       n_electron=256.0, n_state=512, seed=0),
+    "cluster3d-n8192": dict(geometry="cluster", n=8192, per_atom=15, n_atoms=547,
+                            n_electron=2048.0, n_state=1024, seed=1),
+    "cluster3d-n16384": dict(geometry="cluster", n=16384, per_atom=15, n_atoms=1093,
+                             n_electron=4096.0, n_state=2048, seed=2),
 }
 
 
@@ -167,8 +167,9 @@ def chain_problem(n_atoms: int, per_atom: int, seed: int, n_electron: float,
     return Problem(h, s, float(n_electron), int(n_state), f"chain-n{n}-seed{seed}", lam)
 
 
-def config(i: int, tau: float | None = None) -> Problem:
-    c = CONFIGS[i]
+def workload(name: str, tau: float | None = None) -> Problem:
+    """One of WORKLOADS; tau forces lambda_min(S) = tau (the conditioning sweep)."""
+    c = WORKLOADS[name]
     if c["geometry"] == "chain":
         return chain_problem(c["n_atoms"], c["per_atom"], c["seed"], c["n_electron"],
                              c["n_state"])
@@ -176,7 +177,7 @@ def config(i: int, tau: float | None = None) -> Problem:
     pos = cluster_positions(rng, c["n_atoms"])
     h, s, lam = build(rng, pos, c["n"], c["per_atom"],
                       tau=1e-2 if tau is None else tau, force_tau=tau is not None)
-    return Problem(h, s, c["n_electron"], c["n_state"], c["name"], lam)
+    return Problem(h, s, c["n_electron"], c["n_state"], name, lam)
 
 
 def kpoint_problem(n: int, kfrac, seed: int, per_atom: int = 15, density: float = 0.01,

@@ -79,8 +79,8 @@ def test_ev_parity(n, seed, b):
     assert np.abs(r).max() < 1e-9 * scale
 
 
-def test_config0_chain_parity():
-    p = ksinputs.config(0)
+def test_chain512_parity():
+    p = ksinputs.workload("chain-n512")
     ref = oracle.solve(p.h, p.s, p.n_state, p.n_electron)
     out = egb.solve_dm(dev(p.h), dev(p.s), p.n_state, p.n_electron)
     assert rel(out["P"].cpu().numpy(), ref["P"]) <= PW_TOL

@@ -248,15 +248,15 @@ def test_charge_correction_when_bisection_capped():
     np.testing.assert_allclose(f[:20], full[:20], atol=1e-15)
 
 
-# ---------------------------------------------------------------- invariants on config 0
+# ---------------------------------------------------------------- invariants on the 512-function chain
 @pytest.fixture(scope="module")
-def cfg0():
-    p = ksinputs.config(0)
+def chain512():
+    p = ksinputs.workload("chain-n512")
     return p, oracle.solve(p.h, p.s, p.n_state, p.n_electron)
 
 
-def test_config0_vs_lapack(cfg0):
-    p, r = cfg0
+def test_chain512_vs_lapack(chain512):
+    p, r = chain512
     ref_w, ref_v = sla.eigh(p.h, p.s)
     np.testing.assert_allclose(r["eval"], ref_w, rtol=0, atol=1e-11)
     occ = int(p.n_electron // 2)
@@ -264,8 +264,8 @@ def test_config0_vs_lapack(cfg0):
     assert np.linalg.norm(r["P"] - p_ref) / np.linalg.norm(p_ref) < 1e-11
 
 
-def test_config0_invariants(cfg0):
-    p, r = cfg0
+def test_chain512_invariants(chain512):
+    p, r = chain512
     P, W, S, H = r["P"], r["W"], p.s, p.h
     assert abs(np.trace(P @ S) - p.n_electron) < 1e-9
     assert np.linalg.norm(P @ S @ P - 2 * P) / np.linalg.norm(P) < 1e-12
