@@ -87,7 +87,7 @@ int elsi_set_occ_accuracy(elsi_handle h, double occ_accuracy);
 int elsi_set_mu_max_steps(elsi_handle h, int mu_max_steps);
 /* Additions of this library (no counterpart in the paper's keyword list): */
 int elsi_set_precision(elsi_handle h, int precision);      /* ELSI_PREC_* */
-int elsi_set_band_width(elsi_handle h, int band_width);    /* 8..128, multiple of 8 */
+int elsi_set_band_width(elsi_handle h, int band_width);    /* 8..64, multiple of 8 (default 64) */
 /* elsi_customize_elpa, keyword elpa_solver (sec. 4.5): 1 = one-stage tridiagonalisation
  * T = Q^T H~ Q (Eq. 11, first form; blocked Householder with a matrix-vector product per
  * column, memory-bound), 2 = two-stage full -> band -> tridiagonal (default). Applies to
