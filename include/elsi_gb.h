@@ -44,10 +44,12 @@ extern "C" {
 #define ELSI_ERR_NOMEM 9        /* workspace allocation failed */
 #define ELSI_ERR_TOO_LARGE 10   /* request exceeds the fixed scratch of elsi_density_noalloc */
 
-/* Enumerations of elsi_init (sec. 4.3). Only solver 1 (ELPA route), format 1
- * (dense) and either parallel mode (both mean "one GPU, whole matrix") are accepted. */
+/* Enumerations of elsi_init (sec. 4.3). Only solver 1 (ELPA route) is accepted; format 1
+ * (dense) or 2 (CSC: the pattern is set by elsi_set_csc, the dense entry points stay
+ * available); either parallel mode (both mean "one GPU, whole matrix"). */
 #define ELSI_SOLVER_ELPA 1
 #define ELSI_FORMAT_DENSE 1
+#define ELSI_FORMAT_CSC 2    /* PEXSI_CSC: use elsi_set_csc and the _sparse entry points */
 #define ELSI_MODE_MULTI_PROC 1
 #define ELSI_MODE_SINGLE_PROC 2
 

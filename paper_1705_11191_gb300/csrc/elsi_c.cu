@@ -67,7 +67,7 @@ int elsi_init(elsi_handle *out, int solver, int fmt, int mode, int n_basis, int 
     if (!out) return ELSI_ERR_ARG;
     *out = nullptr;
     if (solver != ELSI_SOLVER_ELPA) return ELSI_ERR_UNSUPPORTED;
-    if (fmt != ELSI_FORMAT_DENSE) return ELSI_ERR_UNSUPPORTED;
+    if (fmt != ELSI_FORMAT_DENSE && fmt != ELSI_FORMAT_CSC) return ELSI_ERR_UNSUPPORTED;
     if (mode != ELSI_MODE_MULTI_PROC && mode != ELSI_MODE_SINGLE_PROC) return ELSI_ERR_ARG;
     if (n_basis < 1 || n_state < 1 || n_state > n_basis) return ELSI_ERR_ARG;
     if (!(n_electron >= 0.0) || n_electron > 2.0 * n_state) return ELSI_ERR_ARG;

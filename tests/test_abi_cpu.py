@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_init_rejects_bad_arguments(lib):
     h = ctypes.c_void_p()
     assert lib.elsi_init(ctypes.byref(h), 2, 1, 2, 10, 5, 4.0) == 2   # libOMM: unsupported
-    assert lib.elsi_init(ctypes.byref(h), 1, 2, 2, 10, 5, 4.0) == 2   # CSC: unsupported
+    assert lib.elsi_init(ctypes.byref(h), 1, 3, 2, 10, 5, 4.0) == 2   # unknown format
     assert lib.elsi_init(ctypes.byref(h), 1, 1, 3, 10, 5, 4.0) == 1   # bad mode
     assert lib.elsi_init(ctypes.byref(h), 1, 1, 2, 10, 11, 4.0) == 1  # n_state > n
     assert lib.elsi_init(ctypes.byref(h), 1, 1, 2, 10, 2, 5.0) == 1   # too many electrons
@@ -66,3 +66,27 @@ def test_handle_lifecycle_and_setters(lib):
 def test_stage_names(lib):
     names = egb.stage_names()
     assert names[0] == "cholesky" and "full_to_band" in names and "density" in names
+
+
+def test_customisation_setters_reject_bad_values(lib):
+    h = egb.Handle(16, 8, 8.0)
+    for call, bad in [(h.set_elpa_solver, 3), (h.set_elpa_solver, 0), (h.set_batch_streams, 17),
+                      (h.set_batch_streams, -1), (h.set_sing_check, 3), (h.set_broadening, 5)]:
+        with pytest.raises(egb.ElsiError) as e:
+            call(bad)
+        assert e.value.code == 1
+    with pytest.raises(egb.ElsiError) as e:
+        h.set_sing_check(1, 0.0)  # tolerance must be > 0
+    assert e.value.code == 1
+    h.set_elpa_solver(1)
+    h.set_batch_streams(0)
+    h.set_sing_check(2, 1e-7)
+    h.set_broadening(egb.OCC_MP0, 0.02)
+    assert h.get_n_nonsing() == 16  # no solve yet: the full basis
+    h.close()
+
+
+def test_csc_format_accepted_by_init(lib):
+    h = ctypes.c_void_p()
+    assert lib.elsi_init(ctypes.byref(h), 1, 2, 2, 10, 5, 4.0) == 0
+    assert lib.elsi_finalize(ctypes.byref(h)) == 0
