@@ -34,31 +34,28 @@ __device__ __forceinline__ void report_error(int *status, int code, int aux)
 constexpr long long kSpinLimit = 1ll << 26;
 
 // Grid-wide barrier for cooperative launches (all CTAs co-resident by construction).
-// count/gen live in global memory and are zero before the launch. Returns false if the
-// wait timed out or another CTA reported an error; the caller must then return.
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen,
-                                             unsigned nblocks, int *status)
+// *count lives in global memory, is zero before the launch and only grows: every CTA
+// adds one at each barrier, so barrier number k (k = 1, 2, ...) is passed once the count
+// reaches k * nblocks. Nobody resets the count, which saves the round trips of a
+// generation word. Returns false if the wait timed out or another CTA reported an error;
+// the caller must then return.
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, int *status)
 {
     __shared__ int ok_flag;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned *vgen = gen;
-        unsigned my_gen = *vgen;
         __threadfence();
-        unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            long long it = 0;
-            volatile int *vst = status;
-            while (*vgen == my_gen) {
+        atomicAdd(count, 1u);
+        volatile unsigned *vc = count;
+        volatile int *vst = status;
+        long long it = 0;
+        while (*vc < target) {
+            if ((++it & 255) == 0) {
                 if (vst[ST_CODE] != 0) { ok = 0; break; }
-                if (++it > kSpinLimit) { report_error(status, ELSI_ERR_TIMEOUT, 0); ok = 0; break; }
-                __nanosleep(64);
+                if (it > kSpinLimit) { report_error(status, ELSI_ERR_TIMEOUT, 0); ok = 0; break; }
             }
+            __nanosleep(32);
         }
         __threadfence();
         ok_flag = ok;

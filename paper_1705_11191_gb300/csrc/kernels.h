@@ -98,18 +98,17 @@ template <typename T>
 cudaError_t extract_band(cudaStream_t st, int n, int b, const T *a, int lda, T *band, int ldb);
 
 // ---- tridiagonal eigensolver (sec. 3.1, step 3) ----
-// Eigenvalues il..iu-1 (0-based, ascending) of the symmetric tridiagonal (d, e) by
-// Sturm bisection (w needs count + 4 entries: the Gershgorin bounds follow the values),
-// then eigenvectors of the first kvec of them into z (n x kvec, ldz) as type T.
-// scratch: 2*n*kvec + kvec + 16 doubles.
+// Eigenvalues 0..count-1 (ascending) of the symmetric tridiagonal (d, e) by Sturm
+// bisection (w needs count + 8 entries: the Gershgorin bounds follow the values), then
+// eigenvectors of the first kvec of them into z (n x kvec, ldz) as type T.
+// scratch: 3*n*kvec + kvec + 16 doubles.
 // tol_rel: stop when the bracket is narrower than tol_rel * ||T|| (0: full binary64).
 // Off-diagonals of e below 2 eps ||T|| are set to zero first (T splits into blocks).
 cudaError_t stebz(cudaStream_t st, int n, const double *d, double *e, int count,
                   double *w, int *status, double tol_rel = 0.0);
 template <typename T>
 cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int kvec,
-                  const double *w, T *z, int ldz, double *scratch, int *cluster_ws,
-                  int *status);
+                  const double *w, T *z, int ldz, double *scratch, int *status);
 
 // ---- back-transformations (steps 4 and 5) ----
 template <typename T>

@@ -320,6 +320,9 @@ __global__ void __launch_bounds__(256) q2_apply_tc_kernel(int n, int b, int S, c
 #pragma unroll
                     for (int im = 0; im < 4; ++im) {
                         const int am = im * 16;
+                        // T^T is lower triangular: rows am .. am + 15 have no entry in
+                        // columns >= am + 16
+                        if (k0 >= am + 16) continue;
                         const int i0 = (am + gq) * kWyTLd2 + k0 + tq, i1 = (am + gq + 8) * kWyTLd2 + k0 + tq;
                         const float av[4] = {Ts[i0], Ts[i1], Ts[i0 + 4], Ts[i1 + 4]};
                         unsigned ah[4], al[4];

@@ -417,7 +417,7 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     // binary32-route eigenvalues: the wanted ones are recomputed by the refinement and the
     // rest are reported at the accuracy of this route, so 1e-10 ||T|| suffices
     CKR(stebz(st, n, w.d, w.e, n, w.w, w.status, 1e-10));
-    CKR(stein<float>(st, n, w.d, w.e, n, w.w, X32, n, w.stein, nullptr, w.status));
+    CKR(stein<float>(st, n, w.d, w.e, n, w.w, X32, n, w.stein, w.status));
     CKR(cudaEventRecord(w.ev[STAGE_Q2], st));
     if (!one_stage) CKR(apply_q2_tc(st, n, b, V2, TAU2, n, X32, n, w.q2f));
     CKR(cudaEventRecord(w.ev[STAGE_Q1], st));

@@ -60,7 +60,7 @@ int ensure_workspace(elsi_gb_handle_s *h, int kz)
     ENSURE(w, double, n + 8);
     ENSURE(f, double, n + 8);
     ENSURE(scal, double, 64);
-    ENSURE(stein, double, 2 * n * kz + kz + 64);
+    ENSURE(stein, double, 3 * n * kz + kz + 64);
     ENSURE(sync, unsigned, 64 + 2 * (1024 + 64 + 1024 * 64 + 1024 * 64 * 64));
     ENSURE(status, int, ST_WORDS);
     if (h->precision == ELSI_PREC_FP32_REFINE) {
@@ -157,7 +157,7 @@ static int solve_fp64(elsi_gb_handle_s *h, const SolveRequest &rq)
     // ---- step (3): eigenvalues (all n for ev, the n_state lowest for dm), k vectors
     const int nval = ev_mode ? n : k;
     CK(stebz(st, n, w.d, w.e, nval, w.w, w.status));
-    CK(stein<double>(st, n, w.d, w.e, k, w.w, w.z, n, w.stein, nullptr, w.status));
+    CK(stein<double>(st, n, w.d, w.e, k, w.w, w.z, n, w.stein, w.status));
     CK(cudaEventRecord(w.ev[STAGE_Q2], st));
     // ---- step (4): Z <- Q2 Z
     if (!one_stage) CK(apply_q2<double>(st, n, b, w.v2, w.tau2, k, w.z, n, w.status));

@@ -20,7 +20,7 @@ namespace egb {
 struct PanelArgs {
     int m, bw, rows_per_cta;
     int lda, ldv;
-    unsigned *count, *gen;  // grid barrier state (zeroed)
+    unsigned *count;         // grid barrier counter (zeroed before the launch)
     double *part;            // 2 x gstride partial norms (by column parity)
     double *alpha;           // 2 x 64: row j of the panel (by column parity)
     double *wpart;           // 2 x gstride x 64 partial dot products (by column parity)
@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
     __shared__ double tau_s[64];
     __shared__ double wsum[64];
     __shared__ double colpart[4][64];
+    __shared__ double refl[3];  // beta, tau, 1 / (alpha - beta) of the current column
     const int g = blockIdx.x, G = gridDim.x;
     const int tid = threadIdx.x;
     const int row0 = g * R;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             if (j >= row0 && j < row0 + nrow && tid >= j && tid < bw)
                 prow[tid] = (double)Ploc[(j - row0) * bwp + tid];
         }
-        if (!grid_barrier(a.count, a.gen, G, a.status)) return;
+        if (!grid_barrier(a.count, (unsigned)G * (unsigned)(j + 1), a.status)) return;
         // ---- reflector of column j (every CTA computes the same numbers)
         {
             // sigma2 by warp 0; d_c by 64 column lanes x 4 row groups of CTAs
@@ -93,32 +94,41 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             }
             // L2-coherent loads (written by other CTAs before the barrier), all issued
             // before they are summed
+            // (up to 64 CTAs: all 16 loads of a thread in flight at once)
             double dv = 0.0;
             if (tc > j && tc < bw) {
-                double acc[4] = {0.0, 0.0, 0.0, 0.0};
-                int q = tr;
-                for (; q + 12 < G; q += 16) {
+                double acc[16];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) acc[u] += __ldcg(dpart + (size_t)(q + 4 * u) * 64 + tc);
+                for (int u = 0; u < 16; ++u) {
+                    const int q = tr + 4 * u;
+                    acc[u] = (q < G) ? __ldcg(dpart + (size_t)q * 64 + tc) : 0.0;
                 }
-                for (; q < G; q += 4) acc[0] += __ldcg(dpart + (size_t)q * 64 + tc);
-                dv = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+                for (int q = tr + 64; q < G; q += 4) acc[0] += __ldcg(dpart + (size_t)q * 64 + tc);
+#pragma unroll
+                for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+                    for (int u = 0; u < h; ++u) acc[u] += acc[u + h];
+                dv = acc[0];
             }
             colpart[tr][tc] = dv;
             __syncthreads();
             if (tid < bw) wsum[tid] = colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
+            // the reflector's scalars, once (binary64 arithmetic is scarce on this chip)
+            if (tid == 0) {
+                const double sigma2 = red[0];
+                const double alpha = __ldcg(prow + j);
+                if (sigma2 == 0.0) { refl[0] = alpha; refl[1] = 0.0; refl[2] = 0.0; }
+                else {
+                    const double nrm = sqrt(alpha * alpha + sigma2);
+                    const double bt = (alpha >= 0.0) ? -nrm : nrm;
+                    refl[0] = bt;
+                    refl[1] = (bt - alpha) / bt;
+                    refl[2] = 1.0 / (alpha - bt);
+                }
+            }
             __syncthreads();
         }
-        const double sigma2 = red[0];
-        const double alpha = __ldcg(prow + j);
-        double beta, tau, scl;
-        if (sigma2 == 0.0) { beta = alpha; tau = 0.0; scl = 0.0; }
-        else {
-            double nrm = sqrt(alpha * alpha + sigma2);
-            beta = (alpha >= 0.0) ? -nrm : nrm;
-            tau = (beta - alpha) / beta;
-            scl = 1.0 / (alpha - beta);
-        }
+        const double beta = refl[0], tau = refl[1], scl = refl[2];
         // w_c = P[j][c] + scl d_c; stored pre-multiplied by tau
         if (tid > j && tid < bw) wsum[tid] = tau * (__ldcg(prow + tid) + scl * wsum[tid]);
         __syncthreads();
@@ -171,13 +181,25 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
         }
         a.gram[(size_t)g * bw * bw + e] = (double)s;
     }
-    if (!grid_barrier(a.count, a.gen, G, a.status)) return;
+    if (!grid_barrier(a.count, (unsigned)G * (unsigned)(nref + 1), a.status)) return;
     if (g != 0) return;
     double *gsum = reinterpret_cast<double *>(smem_raw);  // reuse: bw x bw (fits: R*bwp*sizeof(T) >= ...)
     double *tloc = gsum + bw * bw;
+    // (L2-coherent loads of the partials written before the barrier; 8 in flight per
+    // thread)
     for (int e = tid; e < bw * bw; e += blockDim.x) {
         double s = 0.0;
-        for (int q = 0; q < G; ++q) s += ((volatile double *)a.gram)[(size_t)q * bw * bw + e];
+        if (e % bw < e / bw) {  // only G[r][c], r < c, enters the recurrence below
+            double acc[8];
+            int q = 0;
+            for (; q + 8 <= G; q += 8) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] = __ldcg(a.gram + (size_t)(q + u) * bw * bw + e);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s += acc[u];
+            }
+            for (; q < G; ++q) s += __ldcg(a.gram + (size_t)q * bw * bw + e);
+        }
         gsum[e] = s;
         tloc[e] = 0.0;
     }
@@ -257,7 +279,7 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         if ((e = cudaMemsetAsync(sync, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return e;
         PanelArgs pa;
         pa.m = m; pa.bw = bw; pa.rows_per_cta = rows; pa.lda = lda; pa.ldv = n;
-        pa.count = sync; pa.gen = sync + 1;
+        pa.count = sync;
         pa.part = part; pa.alpha = alpha; pa.wpart = wpart; pa.gram = gram; pa.status = status;
         pa.gstride = max_g;
         T *P = a + r0 + (size_t)c0 * lda;

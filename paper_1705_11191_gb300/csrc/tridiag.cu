@@ -2,7 +2,7 @@
 // sec. 3.1), restricted to the wanted eigenpairs as the paper describes for KS-DFT.
 //
 //  * eigenvalues: Sturm-sequence bisection (Givens 1954; Barth, Martin & Wilkinson
-//    1967), one thread per wanted eigenvalue index;
+//    1967), a few threads per wanted eigenvalue index (multisection);
 //  * eigenvectors: one twisted factorisation T - lambda I = N_r D_r N_r^T per
 //    eigenvalue (Parlett & Dhillon 1997/2000), which gives the vector with residual
 //    O(eps ||T||) in O(n) work; one thread per vector;
@@ -36,7 +36,7 @@ __device__ int sturm_count(int n, const double *__restrict__ d, const double *__
     return cnt;
 }
 
-// [0]=gl, [1]=gu, [2]=pivmin, [3]=||T|| bound
+// [0]=gl, [1]=gu, [2]=pivmin, [3]=||T|| bound, [4]=1 if T splits into blocks, else 0
 __global__ void gershgorin_kernel(int n, const double *d, const double *e, double *out)
 {
     __shared__ double red[32];
@@ -67,8 +67,15 @@ __global__ void gershgorin_kernel(int n, const double *d, const double *e, doubl
         out[1] = hi + pad;
         out[2] = DBL_MIN * fmax(1.0, e2max);
         out[3] = tn;
+        red[0] = tn;
     }
-    (void)red;
+    __syncthreads();
+    // [4] = 1 if T splits (an off-diagonal at or below the threshold of split_kernel)
+    const double thr = 2.0 * DBL_EPSILON * red[0];
+    int split = 0;
+    for (int i = threadIdx.x; i < n - 1; i += blockDim.x) split |= (fabs(e[i]) <= thr) ? 1 : 0;
+    split = __syncthreads_or(split);
+    if (threadIdx.x == 0) out[4] = split ? 1.0 : 0.0;
 }
 
 // number of eigenvalues < sigma, binary32 (used only to bracket)
@@ -163,7 +170,7 @@ cudaError_t stebz(cudaStream_t st, int n, const double *d, double *e, int count,
 {
     (void)status;
     if (n <= 0 || count <= 0) return cudaSuccess;
-    // the Gershgorin bounds live right after the count eigenvalues (w has count + 4)
+    // the Gershgorin bounds live right after the count eigenvalues (w has count + 8)
     double *bounds = w + count;
     EGB_COUNT_LAUNCH();
     gershgorin_kernel<<<1, 1024, 0, st>>>(n, d, e, bounds);
@@ -188,6 +195,11 @@ __global__ void block_assign_kernel(int n, const double *d, const double *e, int
 {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= kvec) return;
+    if (bounds[4] == 0.0) {  // T is one block
+        blk[2 * l] = 0;
+        blk[2 * l + 1] = n;
+        return;
+    }
     const double tn = bounds[3], pivmin = bounds[2];
     const double delta = 8.0 * DBL_EPSILON * fmax(fabs(w[l]), tn) + 4.0 * pivmin;
     const double lo = w[l] - delta, hi = w[l] + delta;
@@ -220,58 +232,79 @@ __global__ void block_assign_kernel(int n, const double *d, const double *e, int
     blk[2 * l + 1] = be;
 }
 
-// Twisted factorisation eigenvector for each of the first kvec eigenvalues.
+// One twisted factorisation of T_b - lam I on the block [bs, be): the pivots D+ (dplus)
+// and ratios L+ = e / D+ (lplus) of the forward factorisation, the ratios U- (uminus) of
+// the backward one, the twist index r = argmin |gamma_i| with gamma_r (signed), and
+// ||z||^2 of the vector z with z_r = 1 that solves (T_b - lam I) z = gamma_r e_r.
+// Arrays are indexed [i * kvec + l].
+struct Twist {
+    int r;
+    double gamma, nrm2;
+};
+
+__device__ Twist twisted_factor(const double *__restrict__ d, const double *__restrict__ e,
+                                int bs, int be, double lam, double pivmin, int kvec, int l,
+                                double *dplus, double *lplus, double *uminus)
+{
+    double dp = guard_pivot(d[bs] - lam, pivmin);
+    dplus[(size_t)bs * kvec + l] = dp;
+    for (int i = bs; i < be - 1; ++i) {
+        const double lp = e[i] / dp;
+        lplus[(size_t)i * kvec + l] = lp;
+        dp = guard_pivot(d[i + 1] - lam - lp * e[i], pivmin);
+        dplus[(size_t)(i + 1) * kvec + l] = dp;
+    }
+    double dm = guard_pivot(d[be - 1] - lam, pivmin);
+    Twist t;
+    t.gamma = dplus[(size_t)(be - 1) * kvec + l] + dm - (d[be - 1] - lam);
+    t.r = be - 1;
+    double best = fabs(t.gamma);
+    for (int i = be - 2; i >= bs; --i) {
+        const double um = e[i] / dm;
+        uminus[(size_t)i * kvec + l] = um;
+        dm = guard_pivot(d[i] - lam - um * e[i], pivmin);
+        const double g = dplus[(size_t)i * kvec + l] + dm - (d[i] - lam);
+        if (fabs(g) < best) { best = fabs(g); t.gamma = g; t.r = i; }
+    }
+    double nrm2 = 1.0, zi = 1.0;
+    for (int i = t.r - 1; i >= bs; --i) {
+        zi = -lplus[(size_t)i * kvec + l] * zi;
+        nrm2 += zi * zi;
+    }
+    zi = 1.0;
+    for (int i = t.r; i < be - 1; ++i) {
+        zi = -uminus[(size_t)i * kvec + l] * zi;
+        nrm2 += zi * zi;
+    }
+    t.nrm2 = nrm2;
+    return t;
+}
+
+// Twisted factorisation eigenvector for each of the first kvec eigenvalues (w[l] is the
+// eigenvalue of index l, zero outside its block).
 template <typename T>
 __global__ void twisted_kernel(int n, const double *__restrict__ d, const double *__restrict__ e,
                                int kvec, const double *__restrict__ w, const double *bounds,
                                const int *__restrict__ blk, T *z, int ldz, double *dplus,
-                               double *uminus, int *status)
+                               double *uminus, double *lplus, int *status)
 {
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= kvec) return;
-    const double lam = w[l];
     const double pivmin = bounds[2];
     const int bs = blk[2 * l], be = blk[2 * l + 1];  // the eigenvalue's block [bs, be)
-    // forward: T_b - lam I = L+ D+ L+^T
-    double dp = guard_pivot(d[bs] - lam, pivmin);
-    dplus[(size_t)bs * kvec + l] = dp;
-    for (int i = bs; i < be - 1; ++i) {
-        double lp = e[i] / dp;
-        dp = guard_pivot(d[i + 1] - lam - lp * e[i], pivmin);
-        dplus[(size_t)(i + 1) * kvec + l] = dp;
-    }
-    // backward: T_b - lam I = U- D- U-^T, twist index r = argmin |gamma_r|
-    double dm = guard_pivot(d[be - 1] - lam, pivmin);
-    double best = fabs(dplus[(size_t)(be - 1) * kvec + l] + dm - (d[be - 1] - lam));
-    int r = be - 1;
-    for (int i = be - 2; i >= bs; --i) {
-        double um = e[i] / dm;
-        uminus[(size_t)i * kvec + l] = um;
-        dm = guard_pivot(d[i] - lam - um * e[i], pivmin);
-        double g = fabs(dplus[(size_t)i * kvec + l] + dm - (d[i] - lam));
-        if (g < best) { best = g; r = i; }
-    }
-    // pass 1: norm of z (z_r = 1)
-    double nrm2 = 1.0, zi = 1.0;
-    for (int i = r - 1; i >= bs; --i) {
-        zi = -(e[i] / dplus[(size_t)i * kvec + l]) * zi;
-        nrm2 += zi * zi;
-    }
-    zi = 1.0;
-    for (int i = r; i < be - 1; ++i) {
-        zi = -uminus[(size_t)i * kvec + l] * zi;
-        nrm2 += zi * zi;
-    }
-    if (!(nrm2 < DBL_MAX)) { report_error(status, ELSI_ERR_NO_CONVERGENCE, l); nrm2 = 1.0; }
-    double s = 1.0 / sqrt(nrm2);
-    // pass 2: write z / ||z|| (zero outside the block)
+    const Twist t = twisted_factor(d, e, bs, be, w[l], pivmin, kvec, l, dplus, lplus, uminus);
+    const double nrm2 = t.nrm2;
+    const int r = t.r;
+    if (!(nrm2 < DBL_MAX)) { report_error(status, ELSI_ERR_NO_CONVERGENCE, l); }
+    const double s = (nrm2 < DBL_MAX) ? 1.0 / sqrt(nrm2) : 1.0;
+    // write z / ||z|| (zero outside the block)
     T *zc = z + (size_t)l * ldz;
     for (int i = 0; i < bs; ++i) zc[i] = T(0);
     for (int i = be; i < n; ++i) zc[i] = T(0);
     zc[r] = (T)s;
-    zi = 1.0;
+    double zi = 1.0;
     for (int i = r - 1; i >= bs; --i) {
-        zi = -(e[i] / dplus[(size_t)i * kvec + l]) * zi;
+        zi = -lplus[(size_t)i * kvec + l] * zi;
         zc[i] = (T)(zi * s);
     }
     zi = 1.0;
@@ -399,28 +432,30 @@ __global__ void cluster_orth_kernel(int n, int kvec, const double *w, const doub
 
 template <typename T>
 cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int kvec,
-                  const double *w, T *z, int ldz, double *scratch, int *cluster_ws, int *status)
+                  const double *w, T *z, int ldz, double *scratch, int *status)
 {
-    (void)cluster_ws;
     if (n <= 0 || kvec <= 0) return cudaSuccess;
+    // scratch: D+ (n x kvec), U- (n x kvec), bounds (8), blk (2 kvec ints), L+ (n x kvec)
+    double *dplus = scratch, *uminus = scratch + (size_t)n * kvec;
     double *bounds = scratch + (size_t)2 * n * kvec;
-    int *blk = reinterpret_cast<int *>(bounds + 8);  // 2 * kvec ints
+    int *blk = reinterpret_cast<int *>(bounds + 8);
+    double *lplus = bounds + 16 + kvec;
     EGB_COUNT_LAUNCH();
     gershgorin_kernel<<<1, 1024, 0, st>>>(n, d, e, bounds);
     EGB_COUNT_LAUNCH();
     block_assign_kernel<<<ceil_div(kvec, 64), 64, 0, st>>>(n, d, e, kvec, w, bounds, blk);
     EGB_COUNT_LAUNCH();
-    twisted_kernel<T><<<ceil_div(kvec, 64), 64, 0, st>>>(n, d, e, kvec, w, bounds, blk, z, ldz, scratch,
-                                                        scratch + (size_t)n * kvec, status);
+    twisted_kernel<T><<<ceil_div(kvec, 64), 64, 0, st>>>(n, d, e, kvec, w, bounds, blk, z, ldz, dplus,
+                                                        uminus, lplus, status);
     EGB_COUNT_LAUNCH();
-    cluster_orth_kernel<T><<<kvec, 256, 0, st>>>(n, kvec, w, e, bounds, blk, 1e-5, scratch,
-                                                 scratch + (size_t)n * kvec, z, ldz, status);
+    cluster_orth_kernel<T><<<kvec, 256, 0, st>>>(n, kvec, w, e, bounds, blk, 1e-5, dplus, uminus,
+                                                 z, ldz, status);
     return cudaGetLastError();
 }
 
 template cudaError_t stein<double>(cudaStream_t, int, const double *, const double *, int,
-                                   const double *, double *, int, double *, int *, int *);
+                                   const double *, double *, int, double *, int *);
 template cudaError_t stein<float>(cudaStream_t, int, const double *, const double *, int,
-                                  const double *, float *, int, double *, int *, int *);
+                                  const double *, float *, int, double *, int *);
 
 }  // namespace egb
