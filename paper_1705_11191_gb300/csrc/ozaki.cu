@@ -28,16 +28,35 @@ constexpr int kOzBits = 7;      // bits per digit
 constexpr int kOzBM = 128, kOzBN = 128, kOzBK = 16;  // plane padding: rows, K
 
 // ------------------------------------------------------------------ splitting
+// The digits are those of the binary64 steps r = x 2^-e, then for s = 1..D: t = 128 r,
+// d_s = rint(t), r = t - d_s (every step exact). They are formed here with integer
+// operations on the bit pattern x = +-M 2^E (binary64 arithmetic is scarce on this chip):
+// the running value A_s = sum_{i<=s} d_i 128^{s-i} equals rint(x 2^{7s-e}) (rounding half
+// to even; 128 A_{s-1} is even, so the parity of the ties is the same), hence
+// A_s = +-rne(M / 2^{e-E-7s}) and d_s = A_s - 128 A_{s-1}.
+
+// M / 2^k rounded to nearest, ties to even (M < 2^53, k >= 0).
+__device__ __forceinline__ unsigned long long rne_shift(unsigned long long M, int k)
+{
+    if (k == 0) return M;
+    if (k > 63) return 0ull;  // M < 2^53 < 2^(k-1): below one half
+    unsigned long long q = M >> k;
+    const unsigned long long rem = M & ((1ull << k) - 1ull), half = 1ull << (k - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    return q;
+}
+
 // Vector v (0 <= v < V) has elements x(v, q) = src[v * sv + q * sq], q < K. Writes
 // D digit planes out[s * plane + v * ldo + q] (bf16, q < Kpad, zero padded) and the
-// exponent e_v. Vectors V <= v < Vpad get zero digits. Optional per-element factor
-// scale[q] (a diagonal matrix multiplied in before splitting).
+// exponent e_v (max_q |x(v, q)| = m 2^e_v, m in [0.5, 1)). Vectors V <= v < Vpad get zero
+// digits. Optional per-element factor scale[q] (a diagonal matrix multiplied in before
+// splitting).
 __global__ void ozaki_split_kernel(int V, int Vpad, int K, int Kpad, const double *__restrict__ src,
                                    long long sv, long long sq, const double *__restrict__ scale,
                                    const double *__restrict__ scale2, __nv_bfloat16 *__restrict__ out,
                                    int ldo, size_t plane, int *__restrict__ exps)
 {
-    __shared__ double red[32];
+    __shared__ unsigned long long red[32];
     const int v = blockIdx.x;
     if (v >= Vpad) return;
     __nv_bfloat16 *o = out + (size_t)v * ldo;
@@ -54,29 +73,51 @@ __global__ void ozaki_split_kernel(int V, int Vpad, int K, int Kpad, const doubl
         if (scale2) val *= scale2[q];
         return val;
     };
-    double mx = 0.0;
-    for (int q = threadIdx.x; q < K; q += blockDim.x) mx = fmax(mx, fabs(elem(q)));
-    for (int o2 = 16; o2 > 0; o2 >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    // max |x| as the largest magnitude bit pattern (finite values order like their bits)
+    unsigned long long mb = 0ull;
+    for (int q = threadIdx.x; q < K; q += blockDim.x) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(elem(q)) & 0x7FFFFFFFFFFFFFFFull;
+        mb = b > mb ? b : mb;
+    }
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mb, o2);
+        mb = t > mb ? t : mb;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mb;
     __syncthreads();
     if (threadIdx.x < 32) {
-        double m = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-        for (int o2 = 16; o2 > 0; o2 >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o2));
+        unsigned long long m = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0ull;
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o2);
+            m = t > m ? t : m;
+        }
         if (threadIdx.x == 0) red[0] = m;
     }
     __syncthreads();
-    mx = red[0];
+    mb = red[0];
+    // frexp exponent of the maximum: e = (bit length of M) + E
     int e = 0;
-    if (mx > 0.0) frexp(mx, &e);  // mx = m 2^e, m in [0.5, 1): |x| 2^-e < 1
+    if (mb != 0ull) {
+        const int xf = (int)(mb >> 52);
+        e = xf ? xf - 1022 : (64 - __clzll((long long)(mb & 0xFFFFFFFFFFFFFull))) - 1074;
+    }
     if (threadIdx.x == 0) exps[v] = e;
     for (int q = threadIdx.x; q < Kpad; q += blockDim.x) {
-        double r = (q < K) ? ldexp(elem(q), -e) : 0.0;
+        const unsigned long long u = (q < K) ? (unsigned long long)__double_as_longlong(elem(q)) : 0ull;
+        const int xf = (int)((u >> 52) & 0x7FF);
+        const unsigned long long M = xf ? ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : (u & 0xFFFFFFFFFFFFFull);
+        const int E = xf ? xf - 1075 : -1074;
+        const bool neg = (u >> 63) != 0ull;
+        long long aprev = 0;
 #pragma unroll
-        for (int s = 0; s < kOzD; ++s) {
-            double t = r * (double)(1 << kOzBits);
-            double dgt = rint(t);
-            r = t - dgt;
-            o[(size_t)s * plane + q] = __float2bfloat16((float)dgt);
+        for (int s = 1; s <= kOzD; ++s) {
+            const int k = e - E - kOzBits * s;
+            long long a = 0;
+            if (M != 0ull) a = (long long)(k <= 0 ? (M << (-k)) : rne_shift(M, k));
+            if (neg) a = -a;
+            const long long dgt = a - aprev * (1ll << kOzBits);
+            aprev = a;
+            o[(size_t)(s - 1) * plane + q] = __float2bfloat16(__int2float_rn((int)dgt));
         }
     }
 }
