@@ -220,6 +220,159 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
     }
 }
 
+// ---- W of the two-sided update, fused (three small launches instead of five GEMMs):
+//   X = (A22 V) T,  Y = V^T X,  Z = T^T Y,  W = X - (1/2) V Z.
+// Row blocks of kWRows rows; tiles of 64 x 64 (bw <= 64, zero padded) in shared memory,
+// each of the 256 threads computing a 4 x 4 block of a tile product.
+constexpr int kWRows = 64;
+constexpr int kWLd = 65;
+
+// c[4][4] = sum_k A[r0 + i][k] B[k][c0 + j] for tiles A (64 x kWLd), B (64 x kWLd)
+template <typename T>
+__device__ __forceinline__ void tile_mm(const T *A, const T *B, int kmax, T (&c)[4][4])
+{
+    const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[i][j] = T(0);
+    for (int k = 0; k < kmax; ++k) {
+        T a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = A[(tr + i) * kWLd + k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = B[k * kWLd + tc + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) c[i][j] = fma(a[i], b[j], c[i][j]);
+    }
+}
+
+// tile[i][c] = src[(r0 + i) + c * ld] for i < rows, c < bw; zero elsewhere
+template <typename T>
+__device__ __forceinline__ void load_rows(T *tile, const T *src, int ld, int r0, int rows, int bw)
+{
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int i = e & 63, c = e >> 6;
+        tile[i * kWLd + c] = (i < rows && c < bw) ? src[(size_t)(r0 + i) + (size_t)c * ld] : T(0);
+    }
+}
+
+// X rows = Xa rows T; partial Y (64 x 64 per block, column-major) = V rows^T X rows
+template <typename T>
+__global__ void __launch_bounds__(256) w_stage1_kernel(int m, int bw, const T *xa, const T *V, int ldv,
+                                                       const T *Tm, int ldt, T *X, T *ypart)
+{
+    extern __shared__ unsigned char wsm_raw[];
+    T *sT = reinterpret_cast<T *>(wsm_raw), *sA = sT + 64 * kWLd, *sX = sA + 64 * kWLd;
+    const int r0 = blockIdx.x * kWRows, rows = min(kWRows, m - r0);
+    load_rows(sT, Tm, ldt, 0, bw, bw);
+    load_rows(sA, xa, m, r0, rows, bw);
+    __syncthreads();
+    T c[4][4];
+    tile_mm(sA, sT, bw, c);
+    const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            sX[(tr + i) * kWLd + tc + j] = c[i][j];
+            if (tr + i < rows && tc + j < bw) X[(size_t)(r0 + tr + i) + (size_t)(tc + j) * m] = c[i][j];
+        }
+    __syncthreads();
+    // V rows transposed into sA: sA[a][i] = V[r0 + i][a]
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int i = e & 63, a = e >> 6;
+        sA[a * kWLd + i] = (i < rows && a < bw) ? V[(size_t)(r0 + i) + (size_t)a * ldv] : T(0);
+    }
+    __syncthreads();
+    tile_mm(sA, sX, kWRows, c);
+    T *yp = ypart + (size_t)blockIdx.x * 64 * 64;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) yp[(tr + i) + (tc + j) * 64] = c[i][j];
+}
+
+// Y[e] = sum over blocks g of ypart[g][e] (e < 64 * 64, ascending g)
+template <typename T>
+__global__ void w_stage2_kernel(int nblk, const T *ypart, T *Y)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 64 * 64) return;
+    T s = T(0);
+    int g = 0;
+    for (; g + 8 <= nblk; g += 8) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = ypart[(size_t)(g + u) * 64 * 64 + e];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; g < nblk; ++g) s += ypart[(size_t)g * 64 * 64 + e];
+    Y[e] = s;
+}
+
+// Z = T^T Y (every block, in shared memory); W rows = X rows - (1/2) V rows Z
+template <typename T>
+__global__ void __launch_bounds__(256) w_stage3_kernel(int m, int bw, const T *X, const T *V, int ldv,
+                                                       const T *Tm, int ldt, const T *Y, T *W)
+{
+    extern __shared__ unsigned char wsm_raw[];
+    T *sA = reinterpret_cast<T *>(wsm_raw), *sB = sA + 64 * kWLd, *sZ = sB + 64 * kWLd;
+    const int r0 = blockIdx.x * kWRows, rows = min(kWRows, m - r0);
+    // sA = T^T (sA[a][k] = T[k][a]), sB = Y
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int i = e & 63, c = e >> 6;
+        sA[c * kWLd + i] = (i < bw && c < bw) ? Tm[(size_t)i + (size_t)c * ldt] : T(0);
+        sB[i * kWLd + c] = Y[i + c * 64];
+    }
+    __syncthreads();
+    T c[4][4];
+    tile_mm(sA, sB, bw, c);
+    const int tr = (threadIdx.x >> 4) * 4, tc = (threadIdx.x & 15) * 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sZ[(tr + i) * kWLd + tc + j] = c[i][j];
+    __syncthreads();
+    load_rows(sA, V, ldv, r0, rows, bw);
+    __syncthreads();
+    tile_mm(sA, sZ, bw, c);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (tr + i < rows && tc + j < bw) {
+                const size_t q = (size_t)(r0 + tr + i) + (size_t)(tc + j) * m;
+                W[q] = X[q] - T(0.5) * c[i][j];
+            }
+}
+
+template <typename T>
+static cudaError_t form_w(cudaStream_t st, int m, int bw, const T *xa, const T *V, int ldv,
+                          const T *Tm, int ldt, T *X, T *Y, T *W, T *ypart)
+{
+    const int nblk = ceil_div(m, kWRows);
+    const size_t smem = (size_t)3 * 64 * kWLd * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(w_stage1_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(w_stage3_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    EGB_COUNT_LAUNCH();
+    w_stage1_kernel<T><<<nblk, 256, smem, st>>>(m, bw, xa, V, ldv, Tm, ldt, X, ypart);
+    EGB_COUNT_LAUNCH();
+    w_stage2_kernel<T><<<16, 256, 0, st>>>(nblk, ypart, Y);
+    EGB_COUNT_LAUNCH();
+    w_stage3_kernel<T><<<nblk, 256, smem, st>>>(m, bw, X, V, ldv, Tm, ldt, Y, W);
+    return cudaGetLastError();
+}
+
 size_t sy2sb_work_elems(int n, int b)
 {
     // X (n x b), W (n x b), Y (b x b), Z (b x b)
@@ -299,16 +452,24 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         T *Z = Y + (size_t)b * b;         // b x b
         // X = A22 V
         if ((e = gemm<T>(st, 0, 0, m, bw, m, T(1), A22, lda, V, n, T(0), W, m)) != cudaSuccess) return e;
-        // X = (A22 V) T
-        if ((e = gemm<T>(st, 0, 0, m, bw, bw, T(1), W, m, Tm, ldt, T(0), X, m)) != cudaSuccess) return e;
-        // Y = V^T X
-        if ((e = gemm_splitk<T>(st, 1, 0, bw, bw, m, T(1), V, n, X, m, Y, bw, W,
-                                (size_t)n * b)) != cudaSuccess) return e;
-        // Z = T^T Y
-        if ((e = gemm<T>(st, 1, 0, bw, bw, bw, T(1), Tm, ldt, Y, bw, T(0), Z, bw)) != cudaSuccess) return e;
-        // W = X - 1/2 V Z
-        if ((e = cudaMemcpyAsync(W, X, sizeof(T) * (size_t)m * bw, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
-        if ((e = gemm<T>(st, 0, 0, m, bw, bw, T(-0.5), V, n, Z, bw, T(1), W, m)) != cudaSuccess) return e;
+        if (ceil_div(m, kWRows) + 1 <= max_g) {
+            // X = (A22 V) T, W = X - 1/2 V (T^T (V^T X)); the per-block partials of V^T X
+            // and their sum use the (now idle) Gram scratch of the panel factorisation
+            T *yp = reinterpret_cast<T *>(gram);
+            T *ysum = yp + (size_t)ceil_div(m, kWRows) * 64 * 64;
+            if ((e = form_w<T>(st, m, bw, W, V, n, Tm, ldt, X, ysum, W, yp)) != cudaSuccess) return e;
+        } else {
+            // X = (A22 V) T
+            if ((e = gemm<T>(st, 0, 0, m, bw, bw, T(1), W, m, Tm, ldt, T(0), X, m)) != cudaSuccess) return e;
+            // Y = V^T X
+            if ((e = gemm_splitk<T>(st, 1, 0, bw, bw, m, T(1), V, n, X, m, Y, bw, W,
+                                    (size_t)n * b)) != cudaSuccess) return e;
+            // Z = T^T Y
+            if ((e = gemm<T>(st, 1, 0, bw, bw, bw, T(1), Tm, ldt, Y, bw, T(0), Z, bw)) != cudaSuccess) return e;
+            // W = X - 1/2 V Z
+            if ((e = cudaMemcpyAsync(W, X, sizeof(T) * (size_t)m * bw, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+            if ((e = gemm<T>(st, 0, 0, m, bw, bw, T(-0.5), V, n, Z, bw, T(1), W, m)) != cudaSuccess) return e;
+        }
         // A22 -= V W^T + W V^T   (lower triangle), then mirror. On the tensor-core path the
         // two products are one GEMM over K = 2 bw: [V W] [W V]^T.
         bool done = false;
