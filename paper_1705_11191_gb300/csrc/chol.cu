@@ -85,7 +85,7 @@ static cudaError_t launch_potrf_diag(cudaStream_t st, int jb, T *a, int lda, T *
                                      int *status, int base)
 {
     size_t smem = 2 * sizeof(T) * jb * jb;
-    static bool attr_set = false;  // per instantiation
+    static std::atomic<bool> attr_set{false};  // per instantiation
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(potrf_diag_kernel<T>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,

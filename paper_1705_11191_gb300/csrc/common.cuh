@@ -28,9 +28,10 @@ __device__ __forceinline__ void report_error(int *status, int code, int aux)
     if (atomicCAS(status + ST_CODE, 0, code) == 0) status[ST_AUX] = aux;
 }
 
-// Iteration limit for every spin wait in this library. With a 64 ns back-off this is
-// several seconds, far longer than any legitimate wait; on expiry the waiting kernel
-// records ELSI_ERR_TIMEOUT and returns.
+// Iteration limit for every spin wait in this library. Each iteration backs off for
+// 32-64 ns and reads a word from L2, so the limit is reached after seconds, far longer
+// than any legitimate wait; on expiry the waiting kernel records ELSI_ERR_TIMEOUT and
+// returns.
 constexpr long long kSpinLimit = 1ll << 26;
 
 // Grid-wide barrier for cooperative launches (all CTAs co-resident by construction).

@@ -422,7 +422,7 @@ cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const fl
     const int S = sb2st_steps(n, b);
     const int nblk = (n - 2 + kWyM - 1) / kWyM;
     const size_t tsmem = (size_t)(kWyM * 65 + 3 * kWyM * (kWyM + 1) + kWyM) * sizeof(float);
-    static bool tattr = false;
+    static std::atomic<bool> tattr{false};
     if (!tattr) {
         cudaError_t e = cudaFuncSetAttribute(q2_tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
         if (e != cudaSuccess) return e;
@@ -432,7 +432,7 @@ cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const fl
     q2_tfactor_kernel<<<nblk * S, 128, tsmem, st>>>(n, b, S, nblk, v2, tau2, tfac);
     const size_t smem = (size_t)(kWyCols * kWyRingLd + kWyM * kWyVLd + kWyM * kWyTLd2 +
                                  kWyWarps * kWyWcols * kWyTLd2) * sizeof(float);
-    static bool attr = false;
+    static std::atomic<bool> attr{false};
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(q2_apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

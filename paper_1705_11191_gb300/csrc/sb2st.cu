@@ -295,7 +295,7 @@ cudaError_t sb2st(cudaStream_t st, int n, int b, T *band, int ldb, double *d, do
         a.tmax = 3ll * (n - 3) + (S - 1);
         a.count = sync; a.gen = sync + 1; a.status = status;
         size_t smem = (2 * (size_t)b * (b + 8) + 3 * b) * sizeof(T);
-        static bool attr_set[2] = {false, false};
+        static std::atomic<bool> attr_set[2] = {{false}, {false}};
         int ai = sizeof(T) == 8 ? 0 : 1;
         if (!attr_set[ai]) {
             // opt in once for the largest band width (64)
@@ -486,7 +486,7 @@ cudaError_t apply_q2(cudaStream_t st, int n, int b, const T *v2, const T *tau2, 
     const int S = sb2st_steps(n, b);
     constexpr int kQ2Cols = Q2Cols<T>::v;
     size_t smem = ((size_t)kQ2Cols * kQ2RingLd + 2 * (size_t)kQ2Sweeps * b + 2 * kQ2Sweeps) * sizeof(T);
-    static bool attr_set[2] = {false, false};
+    static std::atomic<bool> attr_set[2] = {{false}, {false}};
     int ai = sizeof(T) == 8 ? 0 : 1;
     if (!attr_set[ai]) {
         const size_t smax =

@@ -356,7 +356,7 @@ static cudaError_t form_w(cudaStream_t st, int m, int bw, const T *xa, const T *
 {
     const int nblk = ceil_div(m, kWRows);
     const size_t smem = (size_t)3 * 64 * kWLd * sizeof(T);
-    static bool attr = false;
+    static std::atomic<bool> attr{false};
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(w_stage1_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
@@ -410,7 +410,7 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         size_t smem = (size_t)rows * (bw + 1) * sizeof(T);
         size_t smem_t = 2 * (size_t)bw * bw * sizeof(double);
         if (smem < smem_t) smem = smem_t;
-        static bool attr_set[2] = {false, false};
+        static std::atomic<bool> attr_set[2] = {{false}, {false}};
         int ai = sizeof(T) == 8 ? 0 : 1;
         if (!attr_set[ai]) {
             if ((e = cudaFuncSetAttribute(panel_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
