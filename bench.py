@@ -25,6 +25,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("KS solves/s (H,S→P,W) at n=16384: FP32+refine vs FP64 GPU, rel err ≤1e-9")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+L2_BYTES = 129 * 2 ** 20  # L2 of the GB300
 # binary64 FMA rate of the chip, derived from unit counts: 152 SMs x 2 DFMA/clk/SM x 2 flop
 FP64_FLOP_PER_CLK = 152 * 2 * 2
 
@@ -134,6 +135,19 @@ def cpu_baseline(n_target: int, sample_n: int = 1024):
                       f"took {dt:.2f} s; scaled by (n/{sample_n})^3 to n={n_target}"}
 
 
+def workload_config(n: int, precision: str, world: int) -> dict:
+    """The config object both arms print: the workload by what it is, with its sizes."""
+    import ksinputs
+    c = ksinputs.WORKLOADS.get(f"cluster3d-n{n}")
+    nel = int(c["n_electron"]) if c else n // 4
+    k = int(c["n_state"]) if c else max(1, -(-nel // 2))
+    gb = n * n * 8 / 1e9
+    l2 = ("inputs (2 x %.2g GB) larger than L2; no flush" % gb) if 2 * n * n * 8 > L2_BYTES else \
+        ("inputs (2 x %.2g GB) within L2" % gb)
+    return {"workload": f"3D-cluster KS problem n={n}, N_el={nel}, n_state={k}, integer occupation",
+            "precision": precision, "parallelism": f"replicas x{world}", "l2": l2}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -149,8 +163,7 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / val, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"3D-cluster KS problem n={args.n}, N_el={args.n // 4}, "
-                                   f"n_state={args.n // 8}"},
+            "config": workload_config(args.n, args.precision, world),
             "cpu_baseline": cb,
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -231,10 +244,8 @@ def main():
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if prec == egb.PREC_FP32_REFINE else "f64", "data": "synthetic",
-           "config": {"workload": f"3D-cluster KS problem n={n}, N_el={int(p.n_electron)}, "
-                                  f"n_state={k}, integer occupation, lambda_min(S)={p.lambda_min_s:.3g}",
-                      "precision": args.precision, "parallelism": f"replicas x{world}",
-                      "l2": "inputs (2 x 2.1 GB) larger than L2; no flush"},
+           "config": workload_config(n, args.precision, world),
+           "lambda_min_s": p.lambda_min_s,
            "stages_ms": {kk: round(v, 3) for kk, v in stages.items()},
            "refine_iters": iters, "orth_err": orth,
            "tflops_algorithmic": algorithmic_flops(n, k) / (ms * 1e-3) / 1e12,
