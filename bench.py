@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the binary64 comparison arm")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--lambda-min", type=float, default=None,
+                    help="force lambda_min(S) to this value (the overlap-conditioning sweep)")
     return ap.parse_args()
 
 
@@ -51,14 +53,15 @@ def dist_env():
     return rank, world, local
 
 
-def workload(n: int):
+def workload(n: int, tau: float | None = None):
     import ksinputs
     if n == 16384:
-        p = ksinputs.workload("cluster3d-n16384")
+        p = ksinputs.workload("cluster3d-n16384", tau=tau)
     elif n == 8192:
-        p = ksinputs.workload("cluster3d-n8192")
+        p = ksinputs.workload("cluster3d-n8192", tau=tau)
     else:
-        p = ksinputs.cluster_problem(n, seed=2)
+        p = ksinputs.cluster_problem(n, seed=2, tau=1e-2 if tau is None else tau,
+                                     force_tau=tau is not None)
     return p
 
 
@@ -135,8 +138,9 @@ def cpu_baseline(n_target: int, sample_n: int = 1024):
                       f"took {dt:.2f} s; scaled by (n/{sample_n})^3 to n={n_target}"}
 
 
-def workload_config(n: int, precision: str, world: int) -> dict:
-    """The config object both arms print: the workload by what it is, with its sizes."""
+def workload_config(n: int, world: int, tau: float | None = None) -> dict:
+    """The config object both arms print: the workload by what it is, with its sizes (the
+    arithmetic of each arm is in its own "dtype" and "route" keys, not in the config)."""
     import ksinputs
     c = ksinputs.WORKLOADS.get(f"cluster3d-n{n}")
     nel = int(c["n_electron"]) if c else n // 4
@@ -144,8 +148,10 @@ def workload_config(n: int, precision: str, world: int) -> dict:
     gb = n * n * 8 / 1e9
     l2 = ("inputs (2 x %.2g GB) larger than L2; no flush" % gb) if 2 * n * n * 8 > L2_BYTES else \
         ("inputs (2 x %.2g GB) within L2" % gb)
-    return {"workload": f"3D-cluster KS problem n={n}, N_el={nel}, n_state={k}, integer occupation",
-            "precision": precision, "parallelism": f"replicas x{world}", "l2": l2}
+    lam = "lambda_min(S) >= 1e-2" if tau is None else f"lambda_min(S) = {tau:g}"
+    return {"workload": f"3D-cluster KS problem n={n}, N_el={nel}, n_state={k}, integer "
+                        f"occupation, {lam}",
+            "parallelism": f"replicas x{world}", "l2": l2}
 
 
 def run_reference(args, rank, world):
@@ -163,7 +169,8 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / val, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.n, args.precision, world),
+            "config": workload_config(args.n, world, args.lambda_min),
+            "route": "binary64 CPU oracle (Cholesky + cyclic Jacobi)",
             "cpu_baseline": cb,
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -191,7 +198,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     prec = egb.PREC_FP32_REFINE if args.precision == "fp32_refine" else egb.PREC_FP64
-    p = workload(args.n)
+    p = workload(args.n, args.lambda_min)
     n, k = p.n, p.n_state
     dev = torch.device("cuda", local)
     H = torch.from_numpy(np.ascontiguousarray(p.h)).to(dev)
@@ -244,10 +251,11 @@ def main():
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if prec == egb.PREC_FP32_REFINE else "f64", "data": "synthetic",
-           "config": workload_config(n, args.precision, world),
+           "config": workload_config(n, world, args.lambda_min),
+           "route": args.precision,
            "lambda_min_s": p.lambda_min_s,
            "stages_ms": {kk: round(v, 3) for kk, v in stages.items()},
-           "refine_iters": iters, "orth_err": orth,
+           "refine_iters": iters, "refine_fell_back_to_fp64": iters == -1, "orth_err": orth,
            "tflops_algorithmic": algorithmic_flops(n, k) / (ms * 1e-3) / 1e12,
            "clocks": cs.summary()}
 
@@ -257,6 +265,9 @@ def main():
     dom = "back_q2" if prec == egb.PREC_FP32_REFINE else max(stages, key=stages.get)
     out["roofline"] = roofline_for(dom, stages[dom], n, k, prec, out["clocks"],
                                    refine_iters=max(iters, 0))
+    out["stages_roofline"] = {st: roofline_for(st, v, n, k, prec, out["clocks"],
+                                               refine_iters=max(iters, 0))
+                              for st, v in stages.items() if v > 0.0}
 
     # binary64 arm and the relative error of P between the two routes
     if not args.no_fp64 and rank == 0 and prec == egb.PREC_FP32_REFINE:
@@ -272,6 +283,9 @@ def main():
         t1.record(stream)
         torch.cuda.synchronize()
         ms64 = t0.elapsed_time(t1)
+        ev32 = hd.get_eval()
+        ev64 = h64.get_eval()
+        out["max_abs_err_eval_vs_fp64"] = float((ev32 - ev64).abs().max())
         relp = float(torch.linalg.norm(P - P64) / torch.linalg.norm(P64))
         relw = float(torch.linalg.norm(W - W64) / torch.linalg.norm(W64))
         out["fp64_gpu"] = {"value": 1000.0 / ms64, "unit": "solves/s", "ms_per_step": ms64,
@@ -311,74 +325,103 @@ def main():
 
 
 # dominant kernel of each stage of the binary32+refinement route (one launch per solve
-# unless noted) and its roofline class
+# unless noted) and the arithmetic it runs on
 _STAGE_KERNEL = {
-    "back_q2": ("q2_apply_tc_kernel", "tensor", "tf32"),
-    "band_to_tri": ("chase_kernel<float>", "hbm", None),
-    "refine": ("ozaki_gemm_tc_kernel (all launches of the stage)", "tensor", "bf16"),
-    "full_to_band": ("gemm_tf32x3_kernel + panel_qr_kernel<float>", "tensor", "tf32"),
-    "back_q1": ("gemm_tf32x3_kernel", "tensor", "tf32"),
-    "standard_form": ("gemm_tf32x3_kernel", "tensor", "tf32"),
-    "tridiag_solve": ("bisect_kernel<2>", "alu", None),
+    "cholesky": ("potrf_diag_kernel + gemm_tf32x3_kernel", "tf32"),
+    "standard_form": ("gemm_tf32x3_kernel (blocked triangular solves)", "tf32"),
+    "full_to_band": ("panel_qr_kernel + w_stage kernels + gemm_tf32x3_kernel", "tf32"),
+    "band_to_tri": ("chase_kernel", None),
+    "tridiag_solve": ("bisect_kernel + twisted_kernel", None),
+    "back_q2": ("q2_apply_tc_kernel", "tf32"),
+    "back_q1": ("gemm_tf32x3_kernel", "tf32"),
+    "back_subst": ("gemm_tf32x3_kernel (blocked triangular solve)", "tf32"),
+    "refine": ("ozaki_gemm_tc_kernel (all launches of the stage)", "bf16"),
+    "occupation": ("occupation_kernel", None),
+    "density": ("ozaki_gemm_tc_kernel (P and W)", "bf16"),
 }
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tf32 / bf16 tensor rates
+OZAKI_PRODUCTS = 28  # bf16 digit products per binary64-accurate product (7 digits, 8 levels)
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh), "of measured"
+    except OSError:
+        return {}, "of fallback"
+
+
+def stage_work(stage: str, n: int, k: int, prec: int, refine_iters: int = 4, band: int = 64):
+    """Algorithmic work of one stage per solve: (amount, unit). Flops follow the count of
+    the hot-path table ((8/3) n^3 + 7 n^2 k in total): Cholesky n^3/3, standard form n^3
+    (the symmetric two-sided solve), full->band 4n^3/3, back-transformations 2n^2 N each and
+    back-substitution n^2 N for the N vectors carried (N = n in the binary32 route, which
+    back-transforms all vectors for the refinement; k in the binary64 route), P and W n^2 k
+    each (symmetric products). The refinement counts its binary64-accurate products per pass
+    (H X, S X: 2n^2 k each; X^T Y_H, X^T Y_S: 2n k^2 each), passes = iterations + the final
+    Rayleigh-Ritz. The bulge chase is counted in bytes of band traffic: per (sweep, step)
+    task the b x b blocks X and D are read and written."""
+    nv = n if prec == 1 else k
+    if stage == "band_to_tri":
+        tasks = sum((n - 2 - j) // band + 1 for j in range(n - 2))
+        return tasks * 4.0 * band * band * (4 if prec == 1 else 8), "bytes"
+    flops = {
+        "cholesky": n ** 3 / 3.0,
+        "standard_form": 1.0 * n ** 3,
+        "full_to_band": 4.0 * n ** 3 / 3.0,
+        "back_q2": 2.0 * n * n * nv,
+        "back_q1": 2.0 * n * n * nv,
+        "back_subst": 1.0 * n * n * nv,
+        "density": 2.0 * n * n * k,
+        "refine": (4.0 * n * n * k + 4.0 * k * k * n) * (refine_iters + 1),
+    }.get(stage)
+    return flops, "flops"
 
 
 def roofline_for(stage: str, stage_ms: float, n: int, k: int, prec: int, clocks: dict,
                  refine_iters: int = 4, band: int = 64):
-    """Roofline entry for the dominant stage: algorithmic work of its launch(es) per solve
-    divided by the stage's device time (CUDA events recorded on the solve stream around
-    the stage). Tensor-core stages take the measured sustained bf16 rate (times the nominal
-    tf32/bf16 ratio for tf32 work); the bulge chase is reported as band traffic against the
-    measured copy bandwidth."""
-    peaks = {}
-    try:
-        with open(PEAKS_FILE) as fh:
-            peaks = json.load(fh)
-        src = "of measured"
-    except OSError:
-        src = "of fallback"
+    """Roofline entry of one stage: its algorithmic work per solve (stage_work) divided by
+    the stage's device time (CUDA events recorded on the solve stream around the stage).
+    Tensor-core stages take the measured sustained bf16 rate of MEASURED_PEAKS.json (times
+    the nominal tf32/bf16 ratio for tf32 work; binary64-accurate Ozaki products are
+    counted as their 28 bf16 digit products); the bulge chase takes band bytes against the
+    measured copy bandwidth; binary64 (SIMT) and ALU-bound stages take the binary64 FMA
+    rate derived from unit counts (152 SMs x 2 DFMA/clk x 2070 MHz)."""
+    peaks, src = _peaks()
     bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
     hbm = peaks.get("hbm_gbs") or 6800.0
-    kern, bound, dt = _STAGE_KERNEL.get(stage, (stage, "latency", None))
-    nv = n if prec == 1 else k  # vectors carried through the back-transformations
-    out = {"stage": stage, "kernel": kern, "traffic": None}
+    kern, dt = _STAGE_KERNEL.get(stage, (stage, None))
+    if prec == 0:
+        dt = None
+    out = {"stage": stage, "kernel": kern, "ms": round(stage_ms, 3), "traffic": None}
     sec = stage_ms * 1e-3
-    if prec == 1 and stage == "band_to_tri":
-        # per (sweep, step) task: read and write the b x b block X and the b x b block D
-        tasks = sum((n - 2 - j) // band + 1 for j in range(n - 2))
-        bytes_ = tasks * 4.0 * band * band * 4
-        ach = bytes_ / sec / 1e9
+    work, unit = stage_work(stage, n, k, prec, refine_iters, band)
+    if unit == "bytes":
+        ach = work / sec / 1e9
         out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
-                   peak_note=f"hbm_gbs {src} (copy bandwidth); band bytes = tasks x 4 b^2 x 4 B")
+                   peak_note=f"hbm_gbs {src} (copy bandwidth); band bytes = tasks x 4 b^2 x elem")
         return out
-    flops = {
-        "cholesky": n ** 3 / 3.0,
-        "standard_form": 2.0 * n ** 3,
-        "full_to_band": 4.0 * n ** 3 / 3.0,
-        "back_q1": 2.0 * n * n * nv,
-        "back_q2": 2.0 * n * n * nv,
-        "back_subst": 1.0 * n * n * nv,
-        "density": 2.0 * n * n * k,
-        # digit products of the binary64-accurate products: 28 bf16 GEMMs per product;
-        # per pass H X, S X (n x k x n) and X^T Y_H, X^T Y_S (k x k x n)
-        "refine": 28 * 2.0 * (2.0 * n * n * k + 2.0 * k * k * n) * (refine_iters + 1),
-    }.get(stage)
-    if flops is None or prec == 0:
+    if work is None or dt is None:
         fp64_peak = FP64_FLOP_PER_CLK * 2070e6 / 1e12
-        f = flops if flops is not None else 0.0
-        ach = f / sec / 1e12 if flops else None
+        ach = work / sec / 1e12 if work else None
         out.update(bound="alu", achieved=ach, peak=fp64_peak, unit="TFLOP/s",
                    frac=(ach / fp64_peak) if ach else None,
-                   peak_note="binary64 FMA rate derived from 152 SMs x 2 DFMA/clk x 2070 MHz")
+                   peak_note="binary64 FMA rate derived from 152 SMs x 2 DFMA/clk x 2070 MHz" +
+                             ("" if work else "; no dense-flop count for this stage"))
         return out
-    peak = bf16 * (TF32_PER_BF16 if dt == "tf32" else 1.0)
-    ach = flops / sec / 1e12
+    if dt == "bf16":
+        tc_work = OZAKI_PRODUCTS * work
+        peak = bf16
+        note = (f"bf16_tflops_sustained {src}; {OZAKI_PRODUCTS} bf16 digit products per "
+                "binary64-accurate flop")
+    else:
+        tc_work = work
+        peak = bf16 * TF32_PER_BF16
+        note = (f"bf16_tflops_sustained {src} x nominal tf32/bf16 ratio 1.1/2.25; tf32 work "
+                "counted once (the three split products are not counted)")
+    ach = tc_work / sec / 1e12
     out.update(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-               peak_note=(f"bf16_tflops_sustained {src}" +
-                          (" x nominal tf32/bf16 ratio 1.1/2.25" if dt == "tf32" else "") +
-                          ("; tf32 work counted once (the three split products are not counted)"
-                           if dt == "tf32" else "; 28 digit products per binary64-accurate product")))
+               algorithmic_tflops=work / sec / 1e12, peak_note=note)
     return out
 
 

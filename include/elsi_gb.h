@@ -135,6 +135,10 @@ int elsi_get_edm_real(elsi_handle h, double *edm);
  * of the last elsi_dm_real call. */
 int elsi_get_mu(elsi_handle h, double *mu);
 int elsi_get_occ(elsi_handle h, double *occ);
+/* The n_state lowest eigenvalues (ascending, device array) that the last elsi_dm_real
+ * call occupied (sec. 4.4 computes them on the way to P; the paper's dm call does not
+ * return them; this accessor is an addition). ELSI_ERR_STATE before a dm solve. */
+int elsi_get_eval(elsi_handle h, double *eval);
 
 /* Same as elsi_dm_real + elsi_get_edm_real but with HOST (pageable or pinned)
  * buffers: copies ham/ovlp in, solves, copies P and W out, on the handle's stream.
@@ -153,18 +157,19 @@ int elsi_get_refine_info(elsi_handle h, int *iters, double *orth_err);
 
 /* Allocation-free density matrices from caller-supplied orbitals (this entry point has
  * no counterpart in the paper). For callers that cannot allocate GPU memory when they
- * need the result: code running during CUDA graph capture, hosts whose GPU memory is
- * owned by another framework's pre-sized pool, loops that forbid allocation after
- * start-up. Computes den_mat = evec diag(occ) evec^T and, if edm is not NULL,
+ * need the result: hosts whose GPU memory is owned by another framework's pre-sized pool
+ * (an allocation outside it can fail or fragment it), and loops that forbid allocation
+ * after start-up (cudaMalloc may synchronise the device and take unbounded time). Computes den_mat = evec diag(occ) evec^T and, if edm is not NULL,
  * edm = evec diag(occ * eval) evec^T (n_basis x n_basis, column-major, symmetric).
  * evec: n_basis x n_state column-major device array; occ, eval: n_state device arrays
  * (eval may be NULL when edm is NULL). All pointers are device pointers; work is
  * enqueued on `stream` (cudaStream_t, NULL = legacy default stream) and the call returns
  * without synchronising. Scratch: a fixed 16 MiB array inside the library
  * (n_basis * n_state <= 2^21); larger requests return ELSI_ERR_TOO_LARGE. No memory is
- * allocated. The first call on each device looks up the array's device address, so
- * make that first call before any stream capture. Calls whose GPU work overlaps in time
- * share the scratch and race. Returns ELSI_OK, ELSI_ERR_ARG, ELSI_ERR_TOO_LARGE or
+ * allocated. The first call on each device looks up the array's device address (and
+ * keeps it for later calls), so make that first call before any stream capture; a call
+ * whose launch fails forgets the address, so that a call after a reset of the device
+ * looks it up again. Calls whose GPU work overlaps in time share the scratch and race. Returns ELSI_OK, ELSI_ERR_ARG, ELSI_ERR_TOO_LARGE or
  * ELSI_ERR_CUDA. */
 int elsi_density_noalloc(int n_basis, int n_state, const double *evec, const double *occ,
                          const double *eval, double *den_mat, double *edm, void *stream);

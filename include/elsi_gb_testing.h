@@ -21,6 +21,19 @@
 extern "C" {
 #endif
 
+/*
+ * elsi_gb_set_spin_limit: iteration limit of the library's SIMT spin waits (the grid
+ *   barrier of the cooperative panel factorisation and the per-sweep progress flags of the
+ *   bulge chase; the mbarrier waits of the tensor-core pipelines keep their own limit).
+ *   A wait that has polled more than `polls` times records ELSI_ERR_TIMEOUT in the
+ *   solve's status word and its kernel returns, so the solve returns ELSI_ERR_TIMEOUT and
+ *   the CUDA context stays usable. Process-wide; read at each launch. Default 2^26
+ *   (seconds); 0 makes every wait that has to wait at all expire. Returns ELSI_ERR_ARG
+ *   for polls < 0. elsi_gb_get_spin_limit returns the limit in force.
+ */
+int elsi_gb_set_spin_limit(long long polls);
+long long elsi_gb_get_spin_limit(void);
+
 size_t elsi_gb_gemm_f32_work(int m, int n, int k);
 int elsi_gb_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const float *A, int lda,
                      const float *B, int ldb, float beta, float *C, int ldc, int uplo,

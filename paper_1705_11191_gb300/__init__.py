@@ -67,6 +67,7 @@ def _declare(lib):
         "elsi_get_edm_complex": ([H, _vp], i),
         "elsi_get_mu": ([H, _dp], i),
         "elsi_get_occ": ([H, _vp], i),
+        "elsi_get_eval": ([H, _vp], i),
         "elsi_dm_real_host": ([H, _vp, _vp, _vp, _vp, _dp], i),
         "elsi_get_stage_times": ([H, ctypes.POINTER(ctypes.c_float), i], i),
         "elsi_stage_name": ([i], ctypes.c_char_p),
@@ -74,6 +75,8 @@ def _declare(lib):
         "elsi_get_last_error": ([H], ctypes.c_char_p),
         "elsi_gb_version": ([], ctypes.c_char_p),
         "elsi_gb_launch_count": ([], ctypes.c_longlong),
+        "elsi_gb_set_spin_limit": ([ctypes.c_longlong], i),
+        "elsi_gb_get_spin_limit": ([], ctypes.c_longlong),
         "elsi_density_noalloc": ([i, i, _vp, _vp, _vp, _vp, _vp, _vp], i),
         "elsi_dm_batched_real": ([H, i, _ip, _ip, _pp, _pp, _dp, _dp, i, _pp, _pp, _dp, _dp], i),
         "elsi_dm_batched_complex": ([H, i, _ip, _ip, _pp, _pp, _dp, _dp, i, _pp, _pp, _dp, _dp], i),
@@ -297,6 +300,13 @@ class Handle:
         f = torch.empty(self.n_state, dtype=torch.float64, device="cuda")
         self._check(self._lib.elsi_get_occ(self._h, _vp(_ptr(f))), "elsi_get_occ")
         return f
+
+    def get_eval(self):
+        """The n_state eigenvalues occupied by the last dm_real call (device tensor)."""
+        import torch
+        w = torch.empty(self.n_state, dtype=torch.float64, device="cuda")
+        self._check(self._lib.elsi_get_eval(self._h, _vp(_ptr(w))), "elsi_get_eval")
+        return w
 
     def dm_real_host(self, ham, ovlp, den, edm=None) -> float:
         """Host-buffer entry point: numpy or pinned torch CPU float64 arrays (n, n)."""

@@ -85,14 +85,12 @@ static cudaError_t launch_potrf_diag(cudaStream_t st, int jb, T *a, int lda, T *
                                      int *status, int base)
 {
     size_t smem = 2 * sizeof(T) * jb * jb;
-    static std::atomic<bool> attr_set{false};  // per instantiation
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(potrf_diag_kernel<T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(2 * sizeof(T) * kTriBlock * kTriBlock));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static PerDeviceOnce attr_set;  // per instantiation
+    cudaError_t e = once_per_device(attr_set, [] {
+        return cudaFuncSetAttribute(potrf_diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(2 * sizeof(T) * kTriBlock * kTriBlock));
+    });
+    if (e != cudaSuccess) return e;
     EGB_COUNT_LAUNCH();
     potrf_diag_kernel<T><<<1, 256, smem, st>>>(jb, a, lda, inv, ldi, status, base);
     return cudaGetLastError();

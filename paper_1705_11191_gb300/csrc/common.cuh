@@ -28,19 +28,24 @@ __device__ __forceinline__ void report_error(int *status, int code, int aux)
     if (atomicCAS(status + ST_CODE, 0, code) == 0) status[ST_AUX] = aux;
 }
 
-// Iteration limit for every spin wait in this library. Each iteration backs off for
-// 32-64 ns and reads a word from L2, so the limit is reached after seconds, far longer
+// Default iteration limit of the SIMT spin waits of this library (the grid barrier of the
+// cooperative kernels and the progress flags of the bulge chase). Each iteration backs off
+// for 32-64 ns and reads a word from L2, so the limit is reached after seconds, far longer
 // than any legitimate wait; on expiry the waiting kernel records ELSI_ERR_TIMEOUT and
-// returns.
+// returns. The limit in force is read on the host at each launch (spin_limit()) and passed
+// to the kernel, so that a test can make a wait run out (elsi_gb_set_spin_limit).
 constexpr long long kSpinLimit = 1ll << 26;
+long long spin_limit();
 
 // Grid-wide barrier for cooperative launches (all CTAs co-resident by construction).
 // *count lives in global memory, is zero before the launch and only grows: every CTA
 // adds one at each barrier, so barrier number k (k = 1, 2, ...) is passed once the count
 // reaches k * nblocks. Nobody resets the count, which saves the round trips of a
-// generation word. Returns false if the wait timed out or another CTA reported an error;
+// generation word. A CTA that has polled the count more than `limit` times records
+// ELSI_ERR_TIMEOUT. Returns false if the wait timed out or another CTA reported an error;
 // the caller must then return.
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, int *status)
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, int *status,
+                                             long long limit)
 {
     __shared__ int ok_flag;
     __syncthreads();
@@ -52,10 +57,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target, i
         volatile int *vst = status;
         long long it = 0;
         while (*vc < target) {
-            if ((++it & 255) == 0) {
-                if (vst[ST_CODE] != 0) { ok = 0; break; }
-                if (it > kSpinLimit) { report_error(status, ELSI_ERR_TIMEOUT, 0); ok = 0; break; }
-            }
+            if (++it > limit) { report_error(status, ELSI_ERR_TIMEOUT, 0); ok = 0; break; }
+            if ((it & 255) == 0 && vst[ST_CODE] != 0) { ok = 0; break; }
             __nanosleep(32);
         }
         __threadfence();
@@ -91,5 +94,26 @@ __device__ __forceinline__ T block_sum(T v, T *red /* >= 32 entries of shared */
 }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// One-time set-up per device (cudaFuncSetAttribute and similar): such a setting applies to
+// the device that is current when it is made, so a process that uses several GPUs has to
+// make it once on each. fn() returns cudaError_t; it runs until it has succeeded once on
+// the current device (two threads may both run it, which is harmless for these settings).
+constexpr int kMaxDevices = 64;
+struct PerDeviceOnce {
+    std::atomic<bool> done[kMaxDevices];
+};
+template <typename F>
+inline cudaError_t once_per_device(PerDeviceOnce &o, F &&fn)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return fn();
+    if (o.done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    e = fn();
+    if (e == cudaSuccess) o.done[dev].store(true, std::memory_order_release);
+    return e;
+}
 
 }  // namespace egb

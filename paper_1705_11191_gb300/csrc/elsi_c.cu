@@ -17,6 +17,9 @@ using namespace egb;
 namespace egb {
 
 std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_spin_limit{kSpinLimit};
+
+long long spin_limit() { return g_spin_limit.load(std::memory_order_relaxed); }
 
 const char *const kStageNames[kNumStages] = {
     "cholesky",  "standard_form", "full_to_band", "band_to_tri", "tridiag_solve",
@@ -60,6 +63,15 @@ extern "C" {
 const char *elsi_gb_version(void) { return "elsi-gb300 0.1"; }
 
 long long elsi_gb_launch_count(void) { return egb::g_launches.load(); }
+
+int elsi_gb_set_spin_limit(long long polls)
+{
+    if (polls < 0) return ELSI_ERR_ARG;
+    egb::g_spin_limit.store(polls, std::memory_order_relaxed);
+    return ELSI_OK;
+}
+
+long long elsi_gb_get_spin_limit(void) { return egb::spin_limit(); }
 
 int elsi_init(elsi_handle *out, int solver, int fmt, int mode, int n_basis, int n_state,
               double n_electron)
@@ -403,6 +415,18 @@ int elsi_get_occ(elsi_handle h, double *occ)
                         h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess)
         return set_error(h, ELSI_ERR_CUDA, "copy of occupations failed");
+    return ELSI_OK;
+}
+
+int elsi_get_eval(elsi_handle h, double *eval)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (!eval) return ELSI_ERR_ARG;
+    if (!h->have_occ) return set_error(h, ELSI_ERR_STATE, "no density-matrix solve yet");
+    if (cudaMemcpyAsync(eval, h->wk.w, sizeof(double) * h->n_state, cudaMemcpyDeviceToDevice,
+                        h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return set_error(h, ELSI_ERR_CUDA, "copy of eigenvalues failed");
     return ELSI_OK;
 }
 

@@ -1,9 +1,8 @@
 // Allocation-free entry point: density matrices from caller-supplied orbitals.
 //
-// Some callers cannot allocate GPU memory at the time they need this result: code that
-// runs while a CUDA graph is being captured (cudaMalloc is not capturable), host codes
+// Some callers cannot allocate GPU memory at the time they need this result: host codes
 // whose memory is owned by a pre-sized pool of another framework, or real-time loops
-// that forbid allocation after start-up. This variant of the P/W contraction therefore
+// that forbid allocation after start-up (cudaMalloc may synchronise the device). This variant of the P/W contraction therefore
 // uses a fixed scratch array that lives in the library image itself instead of a
 // handle workspace.
 //
@@ -59,5 +58,15 @@ extern "C" int elsi_density_noalloc(int n_basis, int n_state, const double *evec
     if (rc) return rc;
     cudaError_t e = egb::density_pw<double>((cudaStream_t)stream, n_basis, n_state, evec, n_basis,
                                            occ, eval, den_mat, edm, static_cast<double *>(scratch));
-    return e == cudaSuccess ? ELSI_OK : ELSI_ERR_CUDA;
+    if (e != cudaSuccess) {
+        // the cached address may belong to a context that no longer exists (a reset of
+        // the device): look it up again on the next call
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevices) {
+            std::lock_guard<std::mutex> lock(g_mu);
+            g_scratch_ptr[dev] = nullptr;
+        }
+        return ELSI_ERR_CUDA;
+    }
+    return ELSI_OK;
 }

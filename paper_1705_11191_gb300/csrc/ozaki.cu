@@ -369,17 +369,27 @@ cudaError_t ozaki_gemm(cudaStream_t st, int m, int n, int k, double alpha,
     size_t te;
     int *ts = nullptr;
     tc_scratch(&tw, &te, &ts);
-    static int *dummy_status = nullptr;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(ozaki_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        SMEM_BYTES);
-        if (attr_err == cudaSuccess) attr_err = cudaMalloc((void **)&dummy_status, 8 * sizeof(int));
-        if (attr_err == cudaSuccess) attr_err = cudaMemset(dummy_status, 0, 8 * sizeof(int));
+    // a status word for calls outside a solve (one per device, kept until exit)
+    static int *dummy_status[kMaxDevices] = {};
+    static PerDeviceOnce once;
+    cudaError_t attr_err = once_per_device(once, [] {
+        int dev = 0;
+        cudaError_t r = cudaGetDevice(&dev);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(ozaki_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (r == cudaSuccess && dev >= 0 && dev < kMaxDevices && !dummy_status[dev]) {
+            int *p = nullptr;
+            r = cudaMalloc((void **)&p, 8 * sizeof(int));
+            if (r == cudaSuccess) r = cudaMemset(p, 0, 8 * sizeof(int));
+            if (r == cudaSuccess) dummy_status[dev] = p;
+        }
+        return r;
     });
     if (attr_err != cudaSuccess) return attr_err;
-    a.status = ts ? ts : dummy_status;
+    int dev_now = 0;
+    cudaGetDevice(&dev_now);
+    a.status = ts ? ts : (dev_now >= 0 && dev_now < kMaxDevices ? dummy_status[dev_now] : nullptr);
+    if (!a.status) return cudaErrorInvalidDevice;
     dim3 grid(mpad / BM, npad / BN);
     EGB_COUNT_LAUNCH();
     ozaki_gemm_tc_kernel<<<grid, 192, SMEM_BYTES, st>>>(maps, a);

@@ -422,22 +422,20 @@ cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const fl
     const int S = sb2st_steps(n, b);
     const int nblk = (n - 2 + kWyM - 1) / kWyM;
     const size_t tsmem = (size_t)(kWyM * 65 + 3 * kWyM * (kWyM + 1) + kWyM) * sizeof(float);
-    static std::atomic<bool> tattr{false};
-    if (!tattr) {
-        cudaError_t e = cudaFuncSetAttribute(q2_tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
-        if (e != cudaSuccess) return e;
-        tattr = true;
-    }
+    static PerDeviceOnce tattr;
+    cudaError_t e = once_per_device(tattr, [&] {
+        return cudaFuncSetAttribute(q2_tfactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem);
+    });
+    if (e != cudaSuccess) return e;
     EGB_COUNT_LAUNCH();
     q2_tfactor_kernel<<<nblk * S, 128, tsmem, st>>>(n, b, S, nblk, v2, tau2, tfac);
     const size_t smem = (size_t)(kWyCols * kWyRingLd + kWyM * kWyVLd + kWyM * kWyTLd2 +
                                  kWyWarps * kWyWcols * kWyTLd2) * sizeof(float);
-    static std::atomic<bool> attr{false};
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(q2_apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static PerDeviceOnce attr;
+    e = once_per_device(attr, [&] {
+        return cudaFuncSetAttribute(q2_apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (e != cudaSuccess) return e;
     (void)tau2;
     EGB_COUNT_LAUNCH();
     q2_apply_tc_kernel<<<ceil_div(k, kWyCols), 256, smem, st>>>(n, b, S, tfac, k, z, ldz);

@@ -5,11 +5,11 @@
 //
 // Sweep j (0 <= j <= n-3) annihilates column j below the subdiagonal and chases the
 // resulting bulge down the band in steps t = 0, 1, ...; step t owns the index window
-// [j+1+(t-1)b, j+(t+1)b]. Step (j, t) of sweep j and step (j+1, t-3) of sweep j+1 touch
-// disjoint windows, and every step of sweep j+1 only needs steps of sweep j that end at
-// least one window earlier, so all steps with the same "time" 3j+t are independent:
-// a persistent cooperative kernel walks the time axis with one grid barrier per time
-// step, each CTA running one (sweep, step) task out of shared memory.
+// [j+1+(t-1)b, j+(t+1)b]. Among the tasks of sweep j-1 only step t+1 overlaps the window
+// of step t of sweep j, so the sweeps run concurrently in a persistent cooperative kernel:
+// CTA g takes sweeps g, g + G, ..., each (sweep, step) task out of shared memory, and
+// before step t of sweep j it waits (bounded spin) on the progress flag of sweep j-1
+// until that sweep has finished step t+1. No grid-wide barrier is involved.
 //
 // Each step stores its Householder reflector (b entries, v[0] = 1) and tau in slot
 // j * S + t (S = steps of sweep 0); the back-transformation applies them in the
@@ -53,6 +53,7 @@ struct ChaseArgs {
     long long tmax;
     unsigned *count, *gen;
     int *status;
+    long long spin_limit;  // polls of a progress-flag wait before ELSI_ERR_TIMEOUT
 };
 
 // Householder vector for x (length L) in shared memory: on return x holds v (v[0]=1),
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(256) chase_kernel(T *band, T *v2, T *tau2, Cha
                     long long it = 0;
                     while (*pv < need) {
                         if (vst[ST_CODE] != 0) { abort_flag = 1; break; }
-                        if (++it > kSpinLimit) {
+                        if (++it > a.spin_limit) {
                             report_error(a.status, ELSI_ERR_TIMEOUT, j);
                             abort_flag = 1;
                             break;
@@ -294,17 +295,15 @@ cudaError_t sb2st(cudaStream_t st, int n, int b, T *band, int ldb, double *d, do
         a.n = n; a.b = b; a.ldb = ldb; a.S = S;
         a.tmax = 3ll * (n - 3) + (S - 1);
         a.count = sync; a.gen = sync + 1; a.status = status;
+        a.spin_limit = spin_limit();
         size_t smem = (2 * (size_t)b * (b + 8) + 3 * b) * sizeof(T);
-        static std::atomic<bool> attr_set[2] = {{false}, {false}};
-        int ai = sizeof(T) == 8 ? 0 : 1;
-        if (!attr_set[ai]) {
-            // opt in once for the largest band width (64)
+        static PerDeviceOnce attr_set;  // per instantiation
+        // opt in once per device for the largest band width (64)
+        err = once_per_device(attr_set, [] {
             const size_t smax = (2 * 64 * 72 + 3 * 64) * sizeof(T);
-            if ((err = cudaFuncSetAttribute(chase_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smax)) != cudaSuccess)
-                return err;
-            attr_set[ai] = true;
-        }
+            return cudaFuncSetAttribute(chase_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+        });
+        if (err != cudaSuccess) return err;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chase_kernel<T>, 256, smem);
         int maxpar = (n - 2 + 1) / 2 + 1;  // upper bound of concurrently active sweeps
@@ -486,16 +485,13 @@ cudaError_t apply_q2(cudaStream_t st, int n, int b, const T *v2, const T *tau2, 
     const int S = sb2st_steps(n, b);
     constexpr int kQ2Cols = Q2Cols<T>::v;
     size_t smem = ((size_t)kQ2Cols * kQ2RingLd + 2 * (size_t)kQ2Sweeps * b + 2 * kQ2Sweeps) * sizeof(T);
-    static std::atomic<bool> attr_set[2] = {{false}, {false}};
-    int ai = sizeof(T) == 8 ? 0 : 1;
-    if (!attr_set[ai]) {
+    static PerDeviceOnce attr_set;  // per instantiation
+    cudaError_t e = once_per_device(attr_set, [] {
         const size_t smax =
             ((size_t)kQ2Cols * kQ2RingLd + 2 * (size_t)kQ2Sweeps * 64 + 2 * kQ2Sweeps) * sizeof(T);
-        cudaError_t e = cudaFuncSetAttribute(apply_q2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smax);
-        if (e != cudaSuccess) return e;
-        attr_set[ai] = true;
-    }
+        return cudaFuncSetAttribute(apply_q2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+    });
+    if (e != cudaSuccess) return e;
     EGB_COUNT_LAUNCH();
     apply_q2_kernel<T><<<ceil_div(k, kQ2Cols), kQ2Cols * kQ2Lanes, smem, st>>>(n, b, S, v2, tau2, k, z, ldz);
     return cudaGetLastError();

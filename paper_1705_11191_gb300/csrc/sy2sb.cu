@@ -27,6 +27,7 @@ struct PanelArgs {
     int gstride;             // >= G
     double *gram;            // G x bw x bw partial Gram matrices
     int *status;
+    long long spin_limit;    // polls of a grid-barrier wait before ELSI_ERR_TIMEOUT
 };
 
 template <typename T>
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             if (j >= row0 && j < row0 + nrow && tid >= j && tid < bw)
                 prow[tid] = (double)Ploc[(j - row0) * bwp + tid];
         }
-        if (!grid_barrier(a.count, (unsigned)G * (unsigned)(j + 1), a.status)) return;
+        if (!grid_barrier(a.count, (unsigned)G * (unsigned)(j + 1), a.status, a.spin_limit)) return;
         // ---- reflector of column j (every CTA computes the same numbers)
         {
             // sigma2 by warp 0; d_c by 64 column lanes x 4 row groups of CTAs
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
         }
         a.gram[(size_t)g * bw * bw + e] = (double)s;
     }
-    if (!grid_barrier(a.count, (unsigned)G * (unsigned)(nref + 1), a.status)) return;
+    if (!grid_barrier(a.count, (unsigned)G * (unsigned)(nref + 1), a.status, a.spin_limit)) return;
     if (g != 0) return;
     double *gsum = reinterpret_cast<double *>(smem_raw);  // reuse: bw x bw (fits: R*bwp*sizeof(T) >= ...)
     double *tloc = gsum + bw * bw;
@@ -356,14 +357,14 @@ static cudaError_t form_w(cudaStream_t st, int m, int bw, const T *xa, const T *
 {
     const int nblk = ceil_div(m, kWRows);
     const size_t smem = (size_t)3 * 64 * kWLd * sizeof(T);
-    static std::atomic<bool> attr{false};
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(w_stage1_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(w_stage3_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static PerDeviceOnce attr;  // per instantiation
+    cudaError_t e = once_per_device(attr, [&] {
+        cudaError_t r = cudaFuncSetAttribute(w_stage1_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(w_stage3_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return r;
+    });
+    if (e != cudaSuccess) return e;
     EGB_COUNT_LAUNCH();
     w_stage1_kernel<T><<<nblk, 256, smem, st>>>(m, bw, xa, V, ldv, Tm, ldt, X, ypart);
     EGB_COUNT_LAUNCH();
@@ -410,13 +411,11 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         size_t smem = (size_t)rows * (bw + 1) * sizeof(T);
         size_t smem_t = 2 * (size_t)bw * bw * sizeof(double);
         if (smem < smem_t) smem = smem_t;
-        static std::atomic<bool> attr_set[2] = {{false}, {false}};
-        int ai = sizeof(T) == 8 ? 0 : 1;
-        if (!attr_set[ai]) {
-            if ((e = cudaFuncSetAttribute(panel_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          200 * 1024)) != cudaSuccess) return e;
-            attr_set[ai] = true;
-        }
+        static PerDeviceOnce attr_set;  // per instantiation
+        e = once_per_device(attr_set, [] {
+            return cudaFuncSetAttribute(panel_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        });
+        if (e != cudaSuccess) return e;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_qr_kernel<T>, 256, smem);
         int max_coresident = per_sm * num_sms;
@@ -435,6 +434,7 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         pa.count = sync;
         pa.part = part; pa.alpha = alpha; pa.wpart = wpart; pa.gram = gram; pa.status = status;
         pa.gstride = max_g;
+        pa.spin_limit = spin_limit();
         T *P = a + r0 + (size_t)c0 * lda;
         T *V = v1 + r0 + (size_t)c0 * n;
         T *Tm = t1 + (size_t)c0 * b;

@@ -311,11 +311,9 @@ cudaError_t tc_gemm_f32_parts(cudaStream_t st, int m, int n, int nparts, const T
     if (!make_map(&maps.a_hi, ahi, m, kp) || !make_map(&maps.a_lo, alo, m, kp) ||
         !make_map(&maps.b_hi, bhi, n, kp) || !make_map(&maps.b_lo, blo, n, kp))
         return cudaErrorNotSupported;
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        SMEM_BYTES);
+    static PerDeviceOnce attr_once;
+    cudaError_t attr_err = once_per_device(attr_once, [] {
+        return cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     });
     if (attr_err != cudaSuccess) return attr_err;
     dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN);

@@ -9,13 +9,17 @@ import pytest
 import paper_1705_11191_gb300 as egb
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "elsi_gb.h")
+HEADERS = [os.path.join(ROOT, "include", "elsi_gb.h"),
+           os.path.join(ROOT, "include", "elsi_gb_testing.h")]
 
 
 def _declared():
-    txt = open(HEADER).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(elsi_\w+)\s*\(", txt)))
+    names = set()
+    for hdr in HEADERS:
+        txt = open(hdr).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(elsi_\w+)\s*\(", txt))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -90,3 +94,16 @@ def test_csc_format_accepted_by_init(lib):
     h = ctypes.c_void_p()
     assert lib.elsi_init(ctypes.byref(h), 1, 2, 2, 10, 5, 4.0) == 0
     assert lib.elsi_finalize(ctypes.byref(h)) == 0
+
+
+def test_spin_limit_setter(lib):
+    """The runtime limit of the SIMT spin waits is host state: set, read back, reject < 0."""
+    old = lib.elsi_gb_get_spin_limit()
+    assert old == 1 << 26
+    try:
+        assert lib.elsi_gb_set_spin_limit(5) == 0
+        assert lib.elsi_gb_get_spin_limit() == 5
+        assert lib.elsi_gb_set_spin_limit(-1) == 1
+        assert lib.elsi_gb_get_spin_limit() == 5
+    finally:
+        assert lib.elsi_gb_set_spin_limit(old) == 0

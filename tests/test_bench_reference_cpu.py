@@ -21,7 +21,8 @@ def test_reference_line_contract():
     assert line["impl"] == "reference"
     assert line["metric"] == bench.METRIC
     assert line["unit"] == "solves/s" and line["higher_is_better"] is True
-    assert line["config"] == bench.workload_config(16384, "fp32_refine", 1)
+    assert line["config"] == bench.workload_config(16384, 1)
+    assert line["dtype"] == "f64"
     assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 0
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]

@@ -1,6 +1,6 @@
 """GPU test of elsi_density_noalloc, the allocation-free entry point for callers that
-cannot allocate GPU memory when they need the density matrices (graph capture, memory
-owned by another framework's pool). It is called through the C ABI (ctypes) and checked
+cannot allocate GPU memory when they need the density matrices (memory owned by another
+framework's pre-sized pool, loops that forbid allocation after start-up). It is called through the C ABI (ctypes) and checked
 against the density matrices of the regular elsi_dm_real / elsi_get_edm_real entry points
 on two calls in a row, within the binary64 parity tolerance (1e-9 relative Frobenius).
 This file is collected last on purpose (test_zz_*)."""
@@ -65,12 +65,29 @@ def test_noalloc_density_matches_dm_real_twice():
         assert rel(W, W_ref) <= TOL
 
 
+def test_noalloc_size_limit_boundary():
+    """n_basis * n_state = 2^21 (the scratch size) is accepted and correct."""
+    n, k = 2048, 1024
+    g = torch.Generator(device="cuda").manual_seed(7)
+    evec_t = torch.randn((k, n), dtype=torch.float64, device="cuda", generator=g) / n ** 0.5
+    f = torch.rand(k, dtype=torch.float64, device="cuda", generator=g) * 2.0
+    ev = torch.randn(k, dtype=torch.float64, device="cuda", generator=g)
+    P = torch.full((n, n), float("nan"), dtype=torch.float64, device="cuda")
+    W = torch.full((n, n), float("nan"), dtype=torch.float64, device="cuda")
+    assert _call(n, k, evec_t, f, ev, P, W) == 0
+    C = evec_t.t()  # n x k
+    # P, W are column-major n x n, i.e. the row-major tensors hold P^T = P
+    assert rel(P, (C * f) @ C.t()) <= TOL
+    assert rel(W, (C * (f * ev)) @ C.t()) <= TOL
+
+
 def test_noalloc_rejects_oversize_and_bad_args():
     lib = egb.load()
     null = ctypes.c_void_p(None)
     x = torch.zeros(8, dtype=torch.float64, device="cuda")
     ptr = ctypes.c_void_p(x.data_ptr())
-    # 2^21 + 1 entries would exceed the fixed scratch
-    assert lib.elsi_density_noalloc(1 << 20, 3, ptr, ptr, ptr, ptr, null, null) == 10
+    # n_basis * n_state = 16257 * 129 = 2^21 + 1 entries: one more than the fixed scratch
+    assert 16257 * 129 == (1 << 21) + 1
+    assert lib.elsi_density_noalloc(16257, 129, ptr, ptr, ptr, ptr, null, null) == 10
     assert lib.elsi_density_noalloc(0, 1, ptr, ptr, ptr, ptr, null, null) == 1
     assert lib.elsi_density_noalloc(4, 2, ptr, ptr, null, ptr, ptr, null) == 1  # edm w/o eval
