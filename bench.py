@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the binary64 comparison arm")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the several-problem workloads (k-point batch, mixed sizes)")
+    ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--lambda-min", type=float, default=None,
                     help="force lambda_min(S) to this value (the overlap-conditioning sweep)")
     return ap.parse_args()
@@ -314,6 +317,9 @@ def main():
                       "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": 2 * n * n * 8,
                       "steps": e2e_steps}
 
+    if not args.no_batch and rank == 0:
+        out["batch_workloads"] = batch_workloads(egb, torch, dev, stream, args.batch_steps)
+
     out["gpu_launches"] = launches
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(n)
@@ -322,6 +328,144 @@ def main():
     hd.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _bucket(n: int) -> int:
+    q = 0
+    while (1 << q) < n:
+        q += 1
+    return 1 << q
+
+
+def batch_workloads(egb, torch, dev, stream, steps: int) -> dict:
+    """The several-problem path (k-points and spin channels, SINGLE_PROC mode) on its two
+    synthetic batches, binary32 + refinement, autotuned reduction and concurrency:
+      kpoints-64x2048: 64 complex Hermitian k-point problems of n = 2048 (Gamma-centred
+        4x4x4 grid, 27 real lattice blocks, seed 3), Fermi-Dirac kT = 0.01 Ha, one
+        chemical potential over all k-points (weights 1/64, N_el = 512 per cell),
+        n_state = 640;
+      mixed-200: 200 real problems, n log-uniform over 256..4096 (sizes seed 4, problem i
+        seed 1000 + i), integer occupation with N_el = n/4 each.
+    One warm-up batch (the autotuner runs on first use), then `steps` timed batches (CUDA
+    events on the solve stream; the mixed batch is timed per size bucket, one batched
+    call per bucket). Parity: one problem per batch / bucket solved alone in the binary32
+    route and in the binary64 route, relative Frobenius error of P between the two."""
+    import ksinputs
+    out = {}
+
+    def ev_pair():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # ---- k-point batch
+    t0 = time.perf_counter()
+    n, nk, kt = 2048, 64, 0.01
+    kset = ksinputs.kpoint_set(n, grid=4, seed=3, device=dev)
+    nel = float(n // 4)
+    nstate = 640
+    hams = [h.transpose(0, 1).contiguous() for (_, h, _, _) in kset]
+    ovls = [s_.transpose(0, 1).contiguous() for (_, _, s_, _) in kset]
+    del kset
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    hd = egb.Handle(n, nstate, nel)
+    hd.set_stream(stream)
+    hd.set_precision(egb.PREC_FP32_REFINE)
+    hd.set_broadening(egb.OCC_FERMI, kt)
+    hd.set_occ_accuracy(1e-12)
+    wts = [1.0 / nk] * nk
+    t1 = time.perf_counter()
+    hd.dm_batched(hams, ovls, [nstate] * nk, nel, weights=wts, shared_mu=True, inputs_colmajor=True)
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t1
+    a, b_ = ev_pair()
+    a.record(stream)
+    for _ in range(steps):
+        P, W, E, mu = hd.dm_batched(hams, ovls, [nstate] * nk, nel, weights=wts, shared_mu=True,
+                                    inputs_colmajor=True)
+    b_.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b_) / steps
+    tune = hd.batch_tuning(n, True)
+    del P, W
+    hd.close()
+    # parity of k-point 0 alone: binary32 route vs binary64 route (own chemical potential)
+    h0 = hams[0].transpose(0, 1).contiguous()
+    s0 = ovls[0].transpose(0, 1).contiguous()
+    res = {}
+    for pr in (egb.PREC_FP32_REFINE, egb.PREC_FP64):
+        with egb.Handle(n, nstate, nel) as h1:
+            h1.set_stream(stream)
+            h1.set_precision(pr)
+            h1.set_broadening(egb.OCC_FERMI, kt)
+            h1.set_occ_accuracy(1e-12)
+            p1, e1 = h1.dm_complex(h0, s0)
+            res[pr] = (p1, e1)
+    relp = float(torch.linalg.norm(res[1][0] - res[0][0]) / torch.linalg.norm(res[0][0]))
+    out["kpoints-64x2048"] = {
+        "problems": nk, "n": n, "complex": True, "n_state": nstate, "kT": kt,
+        "problems_per_s": nk / (ms * 1e-3), "ms_per_batch": ms, "steps": steps,
+        "mu": mu, "first_call_s_including_autotune": first_s, "input_generation_s": gen_s,
+        "tuning": None if tune is None else dict(zip(("band_width", "elpa_solver", "streams"), tune)),
+        "parity_kpoint0_rel_err_P_vs_fp64": relp,
+        "parity_kpoint0_abs_err_energy_vs_fp64": abs(res[1][1] - res[0][1])}
+    del hams, ovls, res, h0, s0
+    torch.cuda.empty_cache()
+
+    # ---- mixed sizes
+    t0 = time.perf_counter()
+    sizes = ksinputs.mixed_sizes(200, seed=4)
+    probs = [ksinputs.cluster_problem_torch(nn, 1000 + i, dev) for i, nn in enumerate(sizes)]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    groups = {}
+    for i, nn in enumerate(sizes):
+        groups.setdefault(_bucket(nn), []).append(i)
+    hd = egb.Handle(4096, 1024, 2048.0)
+    hd.set_stream(stream)
+    hd.set_precision(egb.PREC_FP32_REFINE)
+
+    def run_bucket(idx):
+        return hd.dm_batched([probs[i][0] for i in idx], [probs[i][1] for i in idx],
+                             [probs[i][3] for i in idx], [probs[i][2] for i in idx],
+                             shared_mu=False)
+
+    t1 = time.perf_counter()
+    for bk in sorted(groups):
+        run_bucket(groups[bk])
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t1
+    per = {}
+    total_ms = 0.0
+    for bk in sorted(groups):
+        idx = groups[bk]
+        a, b_ = ev_pair()
+        a.record(stream)
+        for _ in range(steps):
+            P, W, E, mus = run_bucket(idx)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        bms = a.elapsed_time(b_) / steps
+        total_ms += bms
+        i0 = idx[0]
+        with egb.Handle(sizes[i0], probs[i0][3], probs[i0][2]) as h64:
+            h64.set_stream(stream)
+            h64.set_precision(egb.PREC_FP64)
+            p64, _ = h64.dm_real(probs[i0][0].clone(), probs[i0][1])
+        relp = float(torch.linalg.norm(P[0] - p64) / torch.linalg.norm(p64))
+        tune = hd.batch_tuning(bk, False)
+        per[f"n<={bk}"] = {
+            "problems": len(idx), "ms_per_batch": bms, "solves_per_s": len(idx) / (bms * 1e-3),
+            "tuning": None if tune is None else dict(zip(("band_width", "elpa_solver", "streams"), tune)),
+            "parity_rel_err_P_vs_fp64": relp, "parity_problem_n": sizes[i0]}
+        del P, W
+    hd.close()
+    out["mixed-200"] = {"problems": len(sizes), "problems_per_s": len(sizes) / (total_ms * 1e-3),
+                        "ms_per_batch_sum_of_buckets": total_ms, "steps": steps,
+                        "first_calls_s_including_autotune": first_s, "input_generation_s": gen_s,
+                        "buckets": per}
+    del probs
+    torch.cuda.empty_cache()
+    return out
 
 
 # dominant kernel of each stage of the binary32+refinement route (one launch per solve

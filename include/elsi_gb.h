@@ -291,6 +291,22 @@ int elsi_dm_batched_complex(elsi_handle h, int nprob, const int *n_basis, const 
  * own workspace for the largest problem it solves. */
 int elsi_set_batch_streams(elsi_handle h, int streams);
 
+/* Autotuner of the batched calls (no counterpart in the paper; on by default). The first
+ * time a batched call meets a problem size bucket (real-form size N rounded up to a power
+ * of two) on a device, in a precision route, it times the solve of the bucket's first
+ * problem with each candidate reduction (two-stage with band width 32 and 64, one-stage
+ * tridiagonalisation), keeps the fastest, then times 1, 2, 4, 8, 16 concurrent solver
+ * instances of that problem (as many as the free device memory allows) and keeps the
+ * count with the highest throughput. The choice is cached for the process. Settings made
+ * explicitly on the handle (elsi_set_band_width, elsi_set_elpa_solver,
+ * elsi_set_batch_streams) are kept and not tuned. A batch then runs its problems largest
+ * first, each taken by the next free solver instance.
+ * elsi_get_batch_tuning: the choice for problems of n basis functions (cplx: complex), or
+ * ELSI_ERR_STATE if that bucket has not been tuned. */
+int elsi_set_batch_autotune(elsi_handle h, int on);
+int elsi_get_batch_tuning(elsi_handle h, int n, int cplx, int *band_width, int *elpa_solver,
+                          int *streams);
+
 /* Phase 1: eigenpairs of every problem, kept in the handle. eval (device, may be NULL)
  * receives the n_state[i] lowest eigenvalues of each problem, concatenated in problem
  * order (sum_i n_state[i] doubles). */

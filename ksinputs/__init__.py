@@ -240,3 +240,116 @@ def kpoint_problem(n: int, kfrac, seed: int, per_atom: int = 15, density: float 
     ne = float(n // 4)
     return Problem(hk, sk, ne, max(1, int(math.ceil(ne / 2))), f"kpoint-n{n}-seed{seed}",
                    1.0 + alpha * lam)
+
+
+# ---------------------------------------------------------------- batches of problems
+# The two batches of the several-problem path (k-points of a periodic cell; uneven real
+# problems). Draws come from numpy's PCG64 in the order stated; the elementwise
+# construction and the lambda_min(S) rescale run with torch on `device` when one is given
+# (a GPU makes the batch generation fast), else with numpy.
+
+def _lam_min_torch(o, torch):
+    return float(torch.linalg.eigvalsh(o)[0].item())
+
+
+def kpoint_set(n: int, grid: int = 4, seed: int = 3, per_atom: int = 15, density: float = 0.01,
+               tau: float = 1e-2, device=None):
+    """Complex Hermitian problems H(k), S(k) of kpoint_problem(n, k, seed) for the
+    Gamma-centred grid x grid x grid k-points k = (i, j, l) / grid (i slowest), built from one
+    set of 27 real lattice blocks (the same draws as kpoint_problem). Returns a list of
+    (kfrac, H, S, lambda_min(S)) with H, S torch complex128 tensors on `device` (row-major
+    (n, n) tensors of the Hermitian matrices) and N_el = n // 4 per problem."""
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cpu")
+    rng = np.random.default_rng(seed)
+    n_atoms = math.ceil(n / per_atom)
+    pos = cluster_positions(rng, n_atoms, density=density)
+    side = (n_atoms / density) ** (1.0 / 3.0)
+    atom = basis_atoms(n, per_atom)
+    xyz = torch.from_numpy(pos[atom]).to(dev)
+    cells = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
+    done, blocks = set(), []
+    for R in cells:
+        mR = tuple(-x for x in R)
+        if mR in done:
+            continue
+        done.add(R)
+        shift = torch.tensor(R, dtype=torch.float64, device=dev) * side
+        d = torch.cdist(xyz, xyz + shift[None, :], compute_mode="donot_use_mm_for_euclid_dist")
+        u = torch.from_numpy(rng.random((n, n))).to(dev)
+        g = torch.from_numpy(rng.standard_normal((n, n))).to(dev)
+        oR = 0.3 * torch.exp(-d / 1.5) * u
+        hR = -0.5 * torch.exp(-d / 1.2) * (1.0 + 0.1 * g)
+        del d, u, g
+        if R == (0, 0, 0):
+            oR = torch.triu(oR, 1)
+            oR = oR + oR.T
+            hR = torch.triu(hR, 1)
+            hR = hR + hR.T
+        blocks.append((R, hR, oR))
+    hd = torch.from_numpy(rng.uniform(-1.0, 0.5, n)).to(dev)
+    out = []
+    ks = [(i / grid, j / grid, l / grid) for i in range(grid) for j in range(grid)
+          for l in range(grid)]
+    for kf in ks:
+        hk = torch.zeros((n, n), dtype=torch.complex128, device=dev)
+        ok = torch.zeros((n, n), dtype=torch.complex128, device=dev)
+        for R, hR, oR in blocks:
+            if R == (0, 0, 0):
+                hk += hR
+                ok += oR
+            else:
+                ph = complex(np.exp(2j * np.pi * float(np.dot(kf, R))))
+                hk += hR * ph + hR.T * ph.conjugate()
+                ok += oR * ph + oR.T * ph.conjugate()
+        hk.diagonal().copy_(hd.to(torch.complex128))
+        hk = 0.5 * (hk + hk.conj().T)
+        ok = 0.5 * (ok + ok.conj().T)
+        lam = _lam_min_torch(ok, torch)
+        alpha = 1.0 if 1.0 + lam >= tau else (1.0 - tau) / (-lam)
+        sk = alpha * ok
+        sk.diagonal().fill_(1.0)
+        out.append((kf, hk, sk, 1.0 + alpha * lam))
+    return out
+
+
+def mixed_sizes(count: int = 200, seed: int = 4, lo: int = 256, hi: int = 4096):
+    """n_i = round(exp(U(ln lo, ln hi))), i < count, from default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(math.log(lo), math.log(hi), count)
+    return [int(round(math.exp(v))) for v in x]
+
+
+def cluster_problem_torch(n: int, seed: int, device, per_atom: int = 15, tau: float = 1e-2):
+    """cluster_problem(n, seed) with the elementwise construction and the lambda_min(S)
+    rescale on `device` (the same numpy draws in the same order). Returns
+    (H, S, n_electron, n_state, lambda_min(S)) with H, S torch float64 (n, n) tensors
+    (symmetric, so the row-major tensor is also the column-major matrix)."""
+    import torch
+    dev = torch.device(device)
+    rng = np.random.default_rng(seed)
+    n_atoms = math.ceil(n / per_atom)
+    pos = cluster_positions(rng, n_atoms)
+    atom = basis_atoms(n, per_atom)
+    xyz = torch.from_numpy(pos[atom]).to(dev)
+    d = torch.cdist(xyz, xyz, compute_mode="donot_use_mm_for_euclid_dist")
+    same = torch.from_numpy(atom[:, None] == atom[None, :]).to(dev)
+    d = torch.where(same, torch.zeros_like(d), d)
+    u = torch.from_numpy(rng.random((n, n))).to(dev)
+    o = torch.triu(0.3 * torch.exp(-d / 1.5) * u, 1)
+    del u
+    o = o + o.T
+    hd = torch.from_numpy(rng.uniform(-1.0, 0.5, n)).to(dev)
+    g = torch.from_numpy(rng.standard_normal((n, n))).to(dev)
+    h = torch.triu(-0.5 * torch.exp(-d / 1.2) * (1.0 + 0.1 * g), 1)
+    del g, d
+    h = h + h.T
+    h.diagonal().copy_(hd)
+    lam_o = _lam_min_torch(o, torch)
+    alpha = 1.0
+    if 1.0 + lam_o < tau:
+        alpha = (1.0 - tau) / (-lam_o)
+    s = alpha * o
+    s.diagonal().fill_(1.0)
+    ne = float(n // 4)
+    return h, s, ne, max(1, int(math.ceil(ne / 2))), 1.0 + alpha * lam_o

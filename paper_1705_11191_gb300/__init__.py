@@ -88,6 +88,8 @@ def _declare(lib):
         "elsi_set_sing_check": ([H, i], i),
         "elsi_set_elpa_solver": ([H, i], i),
         "elsi_set_batch_streams": ([H, i], i),
+        "elsi_set_batch_autotune": ([H, i], i),
+        "elsi_get_batch_tuning": ([H, i, i, _ip, _ip, _ip], i),
         "elsi_set_csc": ([H, i, _vp, _vp, i], i),
         "elsi_ev_real_sparse": ([H, _vp, _vp, _vp, _vp], i),
         "elsi_dm_real_sparse": ([H, _vp, _vp, _vp, _dp], i),
@@ -364,8 +366,21 @@ class Handle:
         return w
 
     def set_batch_streams(self, streams: int):
-        """Concurrent solves in batched calls (0: chosen by problem size)."""
+        """Concurrent solves in batched calls (0: chosen by the autotuner)."""
         self._check(self._lib.elsi_set_batch_streams(self._h, int(streams)), "elsi_set_batch_streams")
+
+    def set_batch_autotune(self, on: bool):
+        """Per-size tuning of band width, tridiagonalisation and concurrency (default on)."""
+        self._check(self._lib.elsi_set_batch_autotune(self._h, 1 if on else 0), "elsi_set_batch_autotune")
+
+    def batch_tuning(self, n: int, cplx: bool = False):
+        """(band_width, elpa_solver, streams) chosen for problems of size n, or None."""
+        b, s, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        rc = self._lib.elsi_get_batch_tuning(self._h, int(n), 1 if cplx else 0, ctypes.byref(b),
+                                             ctypes.byref(s), ctypes.byref(w))
+        if rc != 0:
+            return None
+        return b.value, s.value, w.value
 
     def set_elpa_solver(self, solver: int):
         """1: one-stage tridiagonalisation, 2: two-stage (default)."""
@@ -418,11 +433,11 @@ class Handle:
         return hb, sb
 
     # ---- several problems (k-points / spin channels) ----
-    def _batch_inputs(self, hams, ovlps, n_states):
+    def _batch_inputs(self, hams, ovlps, n_states, inputs_colmajor=False):
         import torch
         cplx = hams[0].is_complex()
         dt = torch.complex128 if cplx else torch.float64
-        prep = (lambda t: _colmajor(t)) if cplx else (lambda t: t)
+        prep = (lambda t: _colmajor(t)) if (cplx and not inputs_colmajor) else (lambda t: t)
         hs = [prep(t) for t in hams]
         ss = None if ovlps is None else [prep(t) for t in ovlps]
         nprob = len(hs)
@@ -449,12 +464,13 @@ class Handle:
         return ps, ws, pp, wp, fix
 
     def dm_batched(self, hams, ovlps, n_states, n_electron, *, weights=None,
-                   shared_mu: bool = True, want_edm: bool = True):
+                   shared_mu: bool = True, want_edm: bool = True, inputs_colmajor: bool = False):
         """Density matrices of several problems (real float64 or complex128 CUDA tensors).
         shared_mu: one chemical potential, sum_i weights[i] sum_l f_il = n_electron;
-        else n_electron is a list, one per problem. Returns (P list, W list or None,
-        band energies, mu (float, or list))."""
-        cplx, dt, hs, ss, nb, ks, hp, sp = self._batch_inputs(hams, ovlps, n_states)
+        else n_electron is a list, one per problem. inputs_colmajor: complex inputs are
+        already column-major (no copy). Returns (P list, W list or None, band energies,
+        mu (float, or list))."""
+        cplx, dt, hs, ss, nb, ks, hp, sp = self._batch_inputs(hams, ovlps, n_states, inputs_colmajor)
         nprob = len(hs)
         ps, ws, pp, wp, fix = self._batch_outputs(want_edm)
         wts = None if weights is None else (ctypes.c_double * nprob)(*[float(w) for w in weights])

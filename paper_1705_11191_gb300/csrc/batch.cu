@@ -11,8 +11,13 @@
 //      weights (occupation_weighted), or one per problem;
 //   3. batch_dm: P_i = C_i diag(f_i) C_i^H and W_i = C_i diag(f_i eps_i) C_i^H, and the
 //      band energy sum_l f_il eps_il of each problem.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <vector>
@@ -53,6 +58,7 @@ struct BatchState {
     EGB_BUF(double, outs)   // per-problem scalars
     EGB_BUF(int, offs)      // state offsets (nprob + 1)
     EGB_BUF(int, status)
+    EGB_BUF(double, tune)   // eigenpair scratch of the autotuner's trial solves
 #undef EGB_BUF
     double *outs_host = nullptr;  // pinned
     size_t outs_host_cap = 0;
@@ -71,6 +77,58 @@ struct BatchState {
     if (!ensure_buf((void **)&b.name, &b.name##_cap, sizeof(type) * (size_t)(count)))     \
         return set_error(h, ELSI_ERR_NOMEM, "cannot allocate batch %s (%zu bytes)", #name,  \
                          sizeof(type) * (size_t)(count));
+
+// ---- autotuner table: per device, precision route, real/complex and size bucket
+struct TuneVal {
+    int band = 64, solver = 2, workers = 1;
+};
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, TuneVal> g_tune;
+
+static int size_bucket(size_t N)
+{
+    int q = 0;
+    while (((size_t)1 << q) < N) ++q;
+    return q;
+}
+
+static bool tune_get(int dev, int prec, bool cplx, int bucket, TuneVal *v)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(dev, prec, cplx ? 1 : 0, bucket));
+    if (it == g_tune.end()) return false;
+    *v = it->second;
+    return true;
+}
+
+static void tune_put(int dev, int prec, bool cplx, int bucket, const TuneVal &v)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[std::make_tuple(dev, prec, cplx ? 1 : 0, bucket)] = v;
+}
+
+bool batch_tuning_lookup(elsi_gb_handle_s *h, int n, bool cplx, int *band, int *solver, int *workers)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    TuneVal v;
+    if (!tune_get(dev, h->precision, cplx, size_bucket((size_t)(cplx ? 2 : 1) * n), &v)) return false;
+    *band = v.band;
+    *solver = v.solver;
+    *workers = v.workers;
+    return true;
+}
+
+// Concurrency without tuning: 4 instances for real-form sizes up to 4096, 2 up to 8192.
+static int default_workers(size_t N) { return N <= 4096 ? 4 : (N <= 8192 ? 2 : 1); }
+
+// Device memory of one solver instance for real-form size N (workspace of ensure_workspace
+// plus the real-form copies of a complex problem), an upper estimate.
+static double instance_bytes(size_t N, int prec)
+{
+    const double n2 = (double)N * (double)N;
+    return (prec == ELSI_PREC_FP32_REFINE ? 150.0 : 80.0) * n2 + 64.0 * 1048576.0;
+}
 
 static BatchState *batch_state(elsi_gb_handle_s *h)
 {
@@ -172,42 +230,34 @@ int batch_ev(elsi_gb_handle_s *h, int nprob, const int *n_basis, const int *n_st
         BCK(cudaMemcpyAsync(b.offs, off.data(), sizeof(int) * (nprob + 1), cudaMemcpyHostToDevice, h->stream));
         BCK(cudaStreamSynchronize(h->stream));
     }
-    // workers: W solver instances, each with its own stream and host thread (a solve is
-    // synchronous on its host thread); problems i = t, t + W, ... go to worker t
-    size_t nmax = 0;
-    for (auto &it : b.items) nmax = (size_t)(cplx ? 2 : 1) * it.n > nmax ? (size_t)(cplx ? 2 : 1) * it.n : nmax;
-    int W = h->batch_workers;
-    if (W <= 0) W = nmax <= 4096 ? 4 : (nmax <= 8192 ? 2 : 1);
-    if (W > nprob) W = nprob;
-    while ((int)b.workers.size() < W - 1) {
-        BatchWorker wk;
-        wk.sub = new (std::nothrow) elsi_gb_handle_s();
-        if (!wk.sub) return set_error(h, ELSI_ERR_NOMEM, "batch worker");
-        wk.sub->magic = kHandleMagic;
-        if (cudaStreamCreateWithFlags(&wk.stream, cudaStreamNonBlocking) != cudaSuccess) {
-            delete wk.sub;
-            return set_error(h, ELSI_ERR_CUDA, "batch worker stream");
-        }
-        b.workers.push_back(wk);
-    }
-    auto configure = [&](elsi_gb_handle_s *s, cudaStream_t wst) {
+    // Problem order: largest first (longest-processing-time order), each problem taken by
+    // the next free solver instance (worker: own handle, stream and host thread, since a
+    // solve is synchronous on its host thread).
+    std::vector<int> order(nprob);
+    for (int i = 0; i < nprob; ++i) order[i] = i;
+    const int mult = cplx ? 2 : 1;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return b.items[x].n > b.items[y].n; });
+    cudaStream_t st = h->stream;
+    BCK(cudaStreamSynchronize(st));  // inputs produced on the caller's stream are ready
+    int dev = 0;
+    cudaGetDevice(&dev);
+
+    // the configuration of one solve: route settings of the handle, reduction of the tuner
+    auto configure = [&](elsi_gb_handle_s *s, cudaStream_t wst, const TuneVal &tv) {
         s->overlap_is_unit = h->overlap_is_unit;
         s->scheme = h->scheme;
         s->kt = h->kt;
         s->occ_accuracy = h->occ_accuracy;
         s->mu_max_steps = h->mu_max_steps;
         s->precision = h->precision;
-        s->band_width = h->band_width;
-        s->elpa_solver = h->elpa_solver;
+        s->band_width = tv.band;
+        s->elpa_solver = tv.solver;
         s->refine_max_iter = h->refine_max_iter;
         s->stream = wst;
         s->reuse_l = false;
         s->occ_stride = cplx ? 2 : 1;
     };
-    cudaStream_t st = h->stream;
-    BCK(cudaStreamSynchronize(st));  // inputs produced on the caller's stream are ready
-    int dev = 0;
-    cudaGetDevice(&dev);
     struct Result {
         int rc = ELSI_OK;
         std::string msg;
@@ -215,59 +265,226 @@ int batch_ev(elsi_gb_handle_s *h, int nprob, const int *n_basis, const int *n_st
         int refine_min = 1 << 30;
         double orth_max = 0.0;
     };
+    // solve problem i in instance s on stream wst; eigenpairs to (vals, vecs)
+    auto solve_one = [&](elsi_gb_handle_s *s, cudaStream_t wst, int i, const TuneVal &tv,
+                         double *vals, double *vecs, Result &r) -> bool {
+        const BatchItem &it = b.items[i];
+        const size_t N = (size_t)mult * it.n;
+        configure(s, wst, tv);
+        s->n = (int)N;
+        s->n_state = mult * it.k;
+        s->n_electron = 0.0;
+        s->have_l = false;
+        SolveRequest rq;
+        rq.ham = ham[i];
+        rq.ovlp = h->overlap_is_unit ? nullptr : ovlp[i];
+        cudaError_t ce = cudaSuccess;
+        if (cplx) {
+            Workspace &sw = s->wk;
+            if (!ensure_buf((void **)&sw.host_h, &sw.host_h_cap, sizeof(double) * N * N) ||
+                (rq.ovlp && !ensure_buf((void **)&sw.host_s, &sw.host_s_cap, sizeof(double) * N * N))) {
+                r.rc = ELSI_ERR_NOMEM;
+                r.msg = "batch: real-form buffers";
+                return false;
+            }
+            ce = embed_hermitian(wst, it.n, ham[i], sw.host_h);
+            if (ce == cudaSuccess && rq.ovlp) ce = embed_hermitian(wst, it.n, ovlp[i], sw.host_s);
+            rq.ham = sw.host_h;
+            rq.ovlp = rq.ovlp ? sw.host_s : nullptr;
+        }
+        if (ce != cudaSuccess) {
+            r.rc = ELSI_ERR_CUDA;
+            r.msg = cudaGetErrorString(ce);
+            return false;
+        }
+        rq.eval = vals;
+        rq.evec = vecs;
+        const int rc2 = run_solve(s, rq);
+        if (rc2) {
+            r.rc = rc2;
+            r.msg = "batch problem " + std::to_string(i) + ": " + s->last_error;
+            return false;
+        }
+        return true;
+    };
+    auto instance = [&](int t, elsi_gb_handle_s **s, cudaStream_t *wst) {
+        *s = (t == 0) ? b.sub : b.workers[t - 1].sub;
+        *wst = (t == 0) ? st : b.workers[t - 1].stream;
+    };
+    auto add_workers = [&](int W) -> int {
+        while ((int)b.workers.size() < W - 1) {
+            BatchWorker wk;
+            wk.sub = new (std::nothrow) elsi_gb_handle_s();
+            if (!wk.sub) return set_error(h, ELSI_ERR_NOMEM, "batch worker");
+            wk.sub->magic = kHandleMagic;
+            if (cudaStreamCreateWithFlags(&wk.stream, cudaStreamNonBlocking) != cudaSuccess) {
+                delete wk.sub;
+                return set_error(h, ELSI_ERR_CUDA, "batch worker stream");
+            }
+            b.workers.push_back(wk);
+        }
+        return ELSI_OK;
+    };
+    // upper bound of concurrent instances for real-form size N from the free device memory
+    auto mem_workers = [&](size_t N) -> int {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 1;
+        const double per = instance_bytes(N, h->precision);
+        int wm = (int)(0.8 * (double)fr / per) + (int)b.workers.size() + 1;
+        return wm < 1 ? 1 : (wm > 16 ? 16 : wm);
+    };
+
+    // ---- tuning of one size bucket on its first problem i (real-form size N): the
+    // reduction variant with the shortest solve, then the concurrency with the highest
+    // throughput (each instance solves problem i into its own scratch; the times of the
+    // second of two runs count, so that workspace allocation is excluded)
+    auto tune_bucket = [&](int i, size_t N, TuneVal &best) -> int {
+        const BatchItem &it = b.items[i];
+        const size_t K = (size_t)mult * it.k;
+        const int wmax = h->batch_workers > 0 ? h->batch_workers : mem_workers(N);
+        BENSURE(tune, double, (size_t)(wmax > 16 ? 16 : wmax) * (N + N * K));
+        auto scratch = [&](int t, double **vals, double **vecs) {
+            *vals = b.tune + (size_t)t * (N + N * K);
+            *vecs = *vals + N;
+        };
+        auto run_concurrent = [&](int W, const TuneVal &v, double *secs) -> int {
+            int rc = add_workers(W);
+            if (rc) return rc;
+            std::vector<Result> rr(W);
+            for (int rep = 0; rep < 2; ++rep) {
+                const auto t0 = std::chrono::steady_clock::now();
+                std::vector<std::thread> th;
+                auto one = [&](int t) {
+                    cudaSetDevice(dev);
+                    elsi_gb_handle_s *s;
+                    cudaStream_t wst;
+                    instance(t, &s, &wst);
+                    double *vals, *vecs;
+                    scratch(t, &vals, &vecs);
+                    if (solve_one(s, wst, i, v, vals, vecs, rr[t])) {
+                        const cudaError_t ce = cudaStreamSynchronize(wst);
+                        if (ce != cudaSuccess && rr[t].rc == ELSI_OK) {
+                            rr[t].rc = ELSI_ERR_CUDA;
+                            rr[t].msg = cudaGetErrorString(ce);
+                        }
+                    }
+                };
+                for (int t = 1; t < W; ++t) th.emplace_back(one, t);
+                one(0);
+                for (auto &x : th) x.join();
+                *secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                for (int t = 0; t < W; ++t)
+                    if (rr[t].rc) return set_error(h, rr[t].rc, "%s", rr[t].msg.c_str());
+            }
+            return ELSI_OK;
+        };
+        // reduction variants (those set explicitly on the handle are kept)
+        std::vector<TuneVal> cand;
+        const int bands[2] = {32, 64};
+        for (int bw : bands)
+            if (!h->band_set || bw == h->band_width)
+                if (!h->solver_set || h->elpa_solver == 2) cand.push_back(TuneVal{bw, 2, 1});
+        if (!h->solver_set || h->elpa_solver == 1) cand.push_back(TuneVal{h->band_width, 1, 1});
+        if (cand.empty()) cand.push_back(TuneVal{h->band_width, h->elpa_solver, 1});
+        double tbest = 1e300;
+        for (const TuneVal &c : cand) {
+            double sec = 0.0;
+            int rc = run_concurrent(1, c, &sec);
+            if (rc) return rc;
+            if (sec < tbest) { tbest = sec; best.band = c.band; best.solver = c.solver; }
+        }
+        // concurrency
+        best.workers = 1;
+        if (h->batch_workers > 0) {
+            best.workers = h->batch_workers;
+        } else {
+            double thr_best = 1.0 / tbest;
+            for (int W = 2; W <= wmax && W <= 16; W *= 2) {
+                double sec = 0.0;
+                int rc = run_concurrent(W, best, &sec);
+                if (rc) return rc;
+                const double thr = W / sec;
+                if (thr > 1.05 * thr_best) { thr_best = thr; best.workers = W; }
+                else break;
+            }
+        }
+        return ELSI_OK;
+    };
+
+    // ---- autotuning of the size buckets met for the first time
+    const int prec = h->precision;
+    std::vector<TuneVal> tv(nprob);
+    for (int q = 0; q < nprob; ++q) {
+        const int i = order[q];
+        const size_t N = (size_t)mult * b.items[i].n;
+        TuneVal v;
+        const bool known = tune_get(dev, prec, cplx, size_bucket(N), &v);
+        if (!known) {
+            v.band = h->band_width;
+            v.solver = h->elpa_solver;
+            v.workers = h->batch_workers > 0 ? h->batch_workers : default_workers(N);
+            if (h->batch_autotune) {
+                int rc = tune_bucket(i, N, v);
+                if (rc) return rc;
+            }
+            tune_put(dev, prec, cplx, size_bucket(N), v);
+        }
+        if (h->band_set) v.band = h->band_width;
+        if (h->solver_set) v.solver = h->elpa_solver;
+        tv[i] = v;
+    }
+
+    // ---- the batch: concurrency of the bucket with the most work, bounded by memory
+    int W = 1;
+    {
+        double wbest = -1.0;
+        size_t nmax = 0;
+        std::map<int, double> work;
+        for (int i = 0; i < nprob; ++i) {
+            const double N = (double)mult * b.items[i].n;
+            work[size_bucket((size_t)N)] += N * N * N;
+            if ((size_t)N > nmax) nmax = (size_t)N;
+        }
+        for (int i = 0; i < nprob; ++i) {
+            const size_t N = (size_t)mult * b.items[i].n;
+            const double wk = work[size_bucket(N)];
+            if (wk > wbest) { wbest = wk; W = tv[i].workers; }
+        }
+        if (h->batch_workers > 0) W = h->batch_workers;
+        const int wm = mem_workers(nmax);
+        if (W > wm) W = wm;
+        if (W > nprob) W = nprob;
+        if (W < 1) W = 1;
+    }
+    rc = add_workers(W);
+    if (rc) return rc;
     std::vector<Result> res(W);
+    std::atomic<int> next{0};
     auto work = [&](int t) {
         cudaSetDevice(dev);
-        elsi_gb_handle_s *s = (t == 0) ? b.sub : b.workers[t - 1].sub;
-        cudaStream_t wst = (t == 0) ? st : b.workers[t - 1].stream;
-        configure(s, wst);
+        elsi_gb_handle_s *s;
+        cudaStream_t wst;
+        instance(t, &s, &wst);
         Result &r = res[t];
-        for (int i = t; i < nprob; i += W) {
+        for (;;) {
+            const int q = next.fetch_add(1);
+            if (q >= nprob) break;
+            const int i = order[q];
             const BatchItem &it = b.items[i];
-            const size_t N = cplx ? 2 * (size_t)it.n : it.n;
-            s->n = (int)N;
-            s->n_state = cplx ? 2 * it.k : it.k;
-            s->n_electron = 0.0;
-            s->have_l = false;
-            SolveRequest rq;
-            rq.ham = ham[i];
-            rq.ovlp = h->overlap_is_unit ? nullptr : ovlp[i];
-            cudaError_t ce = cudaSuccess;
-            if (cplx) {
-                Workspace &sw = s->wk;
-                if (!ensure_buf((void **)&sw.host_h, &sw.host_h_cap, sizeof(double) * N * N) ||
-                    (rq.ovlp && !ensure_buf((void **)&sw.host_s, &sw.host_s_cap, sizeof(double) * N * N))) {
-                    r.rc = ELSI_ERR_NOMEM;
-                    r.msg = "batch: real-form buffers";
-                    return;
-                }
-                ce = embed_hermitian(wst, it.n, ham[i], sw.host_h);
-                if (ce == cudaSuccess && rq.ovlp) ce = embed_hermitian(wst, it.n, ovlp[i], sw.host_s);
-                rq.ham = sw.host_h;
-                rq.ovlp = rq.ovlp ? sw.host_s : nullptr;
+            if (!solve_one(s, wst, i, tv[i], b.vals + it.off_val, b.vecs + it.off_vec, r)) {
+                next.store(nprob);  // the other instances stop after their current problem
+                return;
             }
+            const cudaError_t ce = cplx ? pair_evals(wst, it.k, b.vals + it.off_val, b.lvl + it.off_lvl)
+                                        : cudaMemcpyAsync(b.lvl + it.off_lvl, b.vals + it.off_val,
+                                                          sizeof(double) * it.k, cudaMemcpyDeviceToDevice, wst);
             if (ce != cudaSuccess) {
                 r.rc = ELSI_ERR_CUDA;
                 r.msg = cudaGetErrorString(ce);
+                next.store(nprob);
                 return;
             }
-            rq.eval = b.vals + it.off_val;
-            rq.evec = b.vecs + it.off_vec;
-            const int rc2 = run_solve(s, rq);
-            if (rc2) {
-                r.rc = rc2;
-                r.msg = "batch problem " + std::to_string(i) + ": " + s->last_error;
-                return;
-            }
-            ce = cplx ? pair_evals(wst, it.k, b.vals + it.off_val, b.lvl + it.off_lvl)
-                      : cudaMemcpyAsync(b.lvl + it.off_lvl, b.vals + it.off_val, sizeof(double) * it.k,
-                                        cudaMemcpyDeviceToDevice, wst);
-            if (ce != cudaSuccess) {
-                r.rc = ELSI_ERR_CUDA;
-                r.msg = cudaGetErrorString(ce);
-                return;
-            }
-            for (int q = 0; q < kNumStages; ++q) r.stage_ms[q] += s->stage_ms[q];
+            for (int q2 = 0; q2 < kNumStages; ++q2) r.stage_ms[q2] += s->stage_ms[q2];
             if (s->refine_iters < r.refine_min) r.refine_min = s->refine_iters;
             if (s->orth_err > r.orth_max) r.orth_max = s->orth_err;
         }
@@ -405,7 +622,8 @@ void free_batch(elsi_gb_handle_s *h)
 {
     if (!h->batch) return;
     BatchState &b = *h->batch;
-    void *bufs[] = {b.vals, b.vecs, b.lvl, b.wts, b.occ, b.occ2, b.emb, b.cw, b.outs, b.offs, b.status};
+    void *bufs[] = {b.vals, b.vecs, b.lvl, b.wts, b.occ, b.occ2, b.emb, b.cw, b.outs, b.offs, b.status,
+                    b.tune};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (b.outs_host) cudaFreeHost(b.outs_host);

@@ -161,6 +161,7 @@ int elsi_set_band_width(elsi_handle h, int b)
     if (check_handle(h)) return ELSI_ERR_STATE;
     if (b < 8 || b > 64 || (b % 8)) return set_error(h, ELSI_ERR_ARG, "band width %d", b);
     h->band_width = b;
+    h->band_set = true;
     return ELSI_OK;
 }
 
@@ -271,11 +272,30 @@ int elsi_set_batch_streams(elsi_handle h, int streams)
     return ELSI_OK;
 }
 
+int elsi_set_batch_autotune(elsi_handle h, int on)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (on != 0 && on != 1) return set_error(h, ELSI_ERR_ARG, "batch autotune %d (0 or 1)", on);
+    h->batch_autotune = on;
+    return ELSI_OK;
+}
+
+int elsi_get_batch_tuning(elsi_handle h, int n, int cplx, int *band_width, int *elpa_solver,
+                          int *streams)
+{
+    if (check_handle(h)) return ELSI_ERR_STATE;
+    if (n < 1 || !band_width || !elpa_solver || !streams) return ELSI_ERR_ARG;
+    if (!egb::batch_tuning_lookup(h, n, cplx != 0, band_width, elpa_solver, streams))
+        return set_error(h, ELSI_ERR_STATE, "no tuning for n = %d yet", n);
+    return ELSI_OK;
+}
+
 int elsi_set_elpa_solver(elsi_handle h, int solver)
 {
     if (check_handle(h)) return ELSI_ERR_STATE;
     if (solver != 1 && solver != 2) return set_error(h, ELSI_ERR_ARG, "elpa_solver %d (1 or 2)", solver);
     h->elpa_solver = solver;
+    h->solver_set = true;
     return ELSI_OK;
 }
 

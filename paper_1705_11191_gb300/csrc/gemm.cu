@@ -123,6 +123,45 @@ bool tc_scratch(float **work, size_t *elems, int **status)
     return t_tc_work != nullptr;
 }
 
+// Scratch of the calling thread for binary64-accurate products on the tensor cores (the
+// Ozaki digit planes and row exponents; set around the binary64 Cholesky of the binary32
+// route, absent elsewhere).
+static thread_local __nv_bfloat16 *t_oz_planes = nullptr;
+static thread_local size_t t_oz_elems = 0;
+static thread_local int *t_oz_exps = nullptr;
+static thread_local size_t t_oz_exp_elems = 0;
+
+void set_f64_tc_scratch(__nv_bfloat16 *planes, size_t elems, int *exps, size_t exp_elems)
+{
+    t_oz_planes = planes;
+    t_oz_elems = elems;
+    t_oz_exps = exps;
+    t_oz_exp_elems = exp_elems;
+}
+
+// C = alpha op(A) op(B) + beta C with binary64-accurate digit products: op(A) split by
+// rows, op(B) by columns (once for A A^T). cudaErrorNotSupported if the scratch is short.
+static cudaError_t gemm_f64_digits(cudaStream_t st, int ta, int tb, int m, int n, int k, double alpha,
+                                   const double *A, int lda, const double *B, int ldb, double beta,
+                                   double *C, int ldc, int uplo)
+{
+    const bool same = A == B && lda == ldb && ta != tb && m == n;
+    const size_t ea = ozaki_split_elems(m, k), eb = same ? 0 : ozaki_split_elems(n, k);
+    const size_t xa = (size_t)ceil_div(m, 128) * 128, xb = same ? 0 : (size_t)ceil_div(n, 128) * 128;
+    if (ea + eb > t_oz_elems || xa + xb > t_oz_exp_elems) return cudaErrorNotSupported;
+    __nv_bfloat16 *ad = t_oz_planes, *bd = same ? t_oz_planes : t_oz_planes + ea;
+    int *xe = t_oz_exps, *ye = same ? t_oz_exps : t_oz_exps + xa;
+    cudaError_t e;
+    // row i of op(A): ta = 0 -> A[i + q lda], ta = 1 -> A[q + i lda]
+    if ((e = ozaki_split(st, m, k, A, ta ? lda : 1, ta ? 1 : lda, nullptr, nullptr, ad, xe)) != cudaSuccess)
+        return e;
+    // column j of op(B): tb = 0 -> B[q + j ldb], tb = 1 -> B[j + q ldb]
+    if (!same &&
+        (e = ozaki_split(st, n, k, B, tb ? 1 : ldb, tb ? ldb : 1, nullptr, nullptr, bd, ye)) != cudaSuccess)
+        return e;
+    return ozaki_gemm(st, m, n, k, alpha, ad, xe, bd, ye, beta, C, ldc, uplo);
+}
+
 template <typename T>
 cudaError_t gemm(cudaStream_t st, int ta, int tb, int m, int n, int k, T alpha, const T *A,
                  int lda, const T *B, int ldb, T beta, T *C, int ldc, int uplo)
@@ -133,6 +172,12 @@ cudaError_t gemm(cudaStream_t st, int ta, int tb, int m, int n, int k, T alpha, 
         if (t_tc_work && k >= 16 && (double)m * n * k >= 4.0e6) {
             cudaError_t e = tc_gemm_f32(st, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
                                         uplo, t_tc_work, t_tc_elems, t_tc_status);
+            if (e != cudaErrorNotSupported) return e;
+        }
+    } else {
+        // binary64 products large enough for the digit products on the tensor cores
+        if (t_oz_planes && k >= 32 && (double)m * n * k >= 1.6e7) {
+            cudaError_t e = gemm_f64_digits(st, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, uplo);
             if (e != cudaErrorNotSupported) return e;
         }
     }

@@ -35,6 +35,11 @@ bool tc_scratch(float **work, size_t *elems, int **status);
 // Routes this thread's binary32 gemm() calls with large enough shapes to tc_gemm_f32 with
 // the given scratch (work = nullptr: SIMT kernel only).
 void set_tc_scratch(float *work, size_t elems, int *status);
+// Routes this thread's binary64 gemm() calls with large enough shapes to binary64-accurate
+// digit products on the tensor cores (ozaki_split + ozaki_gemm) with the given digit-plane
+// and exponent scratch (planes = nullptr: SIMT binary64 kernel only). Uses the status word
+// of set_tc_scratch for timeouts.
+void set_f64_tc_scratch(__nv_bfloat16 *planes, size_t elems, int *exps, size_t exp_elems);
 cudaError_t tc_gemm_f32(cudaStream_t st, int ta, int tb, int m, int n, int k, float alpha,
                         const float *A, int lda, const float *B, int ldb, float beta, float *C,
                         int ldc, int uplo, float *work, size_t work_elems, int *status);
@@ -114,11 +119,16 @@ cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int 
 template <typename T>
 cudaError_t apply_q2(cudaStream_t st, int n, int b, const T *v2, const T *tau2, int k,
                      T *z, int ldz, int *status);
-// binary32 Z <- Q2 Z with compact-WY groups on the tensor cores (q2wy.cu); tfac: scratch of
-// q2_tfactor_elems(n, b) floats.
-size_t q2_tfactor_elems(int n, int b);
+// binary32 Z <- Q2 Z with compact-WY groups of 64 reflectors on the tcgen05 tensor cores
+// (q2tc.cu); fac: scratch of q2_factor_elems(n, b) floats (16-byte aligned) for the
+// per-group operand blocks; b a multiple of 8 in 8..64. Timeouts of its bounded waits go
+// to status (ELSI_ERR_TIMEOUT).
+size_t q2_factor_elems(int n, int b);
 cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const float *tau2, int k,
-                        float *z, int ldz, float *tfac);
+                        float *z, int ldz, float *fac, int *status);
+size_t q2_tfactor_elems_legacy(int n, int b);
+cudaError_t apply_q2_tc_legacy(cudaStream_t st, int n, int b, const float *v2, const float *tau2, int k,
+                               float *z, int ldz, float *tfac);
 // Z <- Q1 Z in groups of kQ1Group panels; work: q1_work_elems(b, k) elements.
 constexpr int kQ1Group = 4;
 inline size_t q1_work_elems(int b, int k)

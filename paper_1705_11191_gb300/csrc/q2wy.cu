@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(256) q2_apply_tc_kernel(int n, int b, int S, c
     asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
-size_t q2_tfactor_elems(int n, int b)
+size_t q2_tfactor_elems_legacy(int n, int b)
 {
     if (n < 3) return 1;
     const int S = sb2st_steps(n, b);
@@ -414,7 +414,7 @@ size_t q2_tfactor_elems(int n, int b)
     return (size_t)nblk * S * kWyGroupWords;
 }
 
-cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const float *tau2, int k,
+cudaError_t apply_q2_tc_legacy(cudaStream_t st, int n, int b, const float *v2, const float *tau2, int k,
                         float *z, int ldz, float *tfac)
 {
     if (n < 3 || k <= 0) return cudaSuccess;

@@ -368,24 +368,21 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
 
     CKR(cudaEventRecord(w.ev[STAGE_CHOL], st));
     if (!unit && !(h->reuse_l && h->have_l && h->have_l_prec == ELSI_PREC_FP32_REFINE)) {
+        // Eq. 8 in binary64: the overlap may be ill-conditioned, and a factor that is accurate
+        // in binary64 keeps the binary32 stages' start as good as binary32 allows. The
+        // trailing updates of the blocked factorisation run as binary64-accurate digit
+        // products on the tensor cores; the factor and the inverses of its diagonal blocks
+        // are then rounded to binary32 for the standard form and the back-substitution.
         CKR(check_finite<double>(st, n, n, rq.ovlp, n, w.status));
-        CKR(copy_matrix<float, double>(st, n, n, rq.ovlp, n, L, n));
-        CKR(potrf<float>(st, n, L, n, INVD, WORK, w.status));
-        // An S that is positive definite in binary64 may not be in binary32: then factor
-        // in binary64 and round the factor.
-        int code = 0;
-        CKR(cudaMemcpyAsync(w.status_host, w.status, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, st));
-        CKR(cudaStreamSynchronize(st));
-        code = w.status_host[ST_CODE];
-        if (code == ELSI_ERR_NOT_PD) {
-            CKR(cudaMemsetAsync(w.status, 0, sizeof(int) * ST_WORDS, st));
-            double *L64 = w.a;  // scratch
-            double *INV64 = reinterpret_cast<double *>(w.stein);
-            CKR(copy_matrix<double, double>(st, n, n, rq.ovlp, n, L64, n));
-            CKR(potrf<double>(st, n, L64, n, INV64, w.edm, w.status));
-            CKR(copy_matrix<float, double>(st, n, n, L64, n, L, n));
-            CKR(copy_matrix<float, double>(st, n, kTriBlock, INV64, n, INVD, n));
-        }
+        double *L64 = w.v1;                                        // n x n, free until full->band
+        double *INV64 = reinterpret_cast<double *>(w.stein);       // n x kTriBlock
+        CKR(copy_matrix<double, double>(st, n, n, rq.ovlp, n, L64, n));
+        set_f64_tc_scratch(w.oz, w.oz_cap / sizeof(__nv_bfloat16), w.ozexp, w.ozexp_cap / sizeof(int));
+        cudaError_t pe = potrf<double>(st, n, L64, n, INV64, w.edm, w.status);
+        set_f64_tc_scratch(nullptr, 0, nullptr, 0);
+        CKR(pe);
+        CKR(copy_matrix<float, double>(st, n, n, L64, n, L, n));
+        CKR(copy_matrix<float, double>(st, n, kTriBlock, INV64, n, INVD, n));
         h->have_l_prec = ELSI_PREC_FP32_REFINE;
     }
     CKR(cudaEventRecord(w.ev[STAGE_STDFORM], st));
@@ -419,7 +416,7 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     CKR(stebz(st, n, w.d, w.e, n, w.w, w.status, 1e-10));
     CKR(stein<float>(st, n, w.d, w.e, n, w.w, X32, n, w.stein, w.status));
     CKR(cudaEventRecord(w.ev[STAGE_Q2], st));
-    if (!one_stage) CKR(apply_q2_tc(st, n, b, V2, TAU2, n, X32, n, w.q2f));
+    if (!one_stage) CKR(apply_q2_tc(st, n, b, V2, TAU2, n, X32, n, w.q2f, w.status));
     CKR(cudaEventRecord(w.ev[STAGE_Q1], st));
     if (one_stage) CKR(apply_q_onestage<float>(st, n, n, V1, T1, X32, n, WORK));
     else CKR(apply_q1<float>(st, n, b, n, V1, T1, X32, n, WORK));

@@ -72,7 +72,7 @@ int ensure_workspace(elsi_gb_handle_s *h, int kz)
                                       3 * ozaki_split_elems((int)k, (int)n) +
                                       3 * ozaki_split_elems((int)n, (int)k));
         ENSURE(ozexp, int, 8 * (n + k + 256));
-        ENSURE(q2f, float, q2_tfactor_elems((int)n, b));
+        ENSURE(q2f, float, q2_factor_elems((int)n, b));
         ENSURE(tcw, float, tc_gemm_work_elems((int)n, (int)n, (int)n));
     }
     if (!w.status_host && cudaMallocHost((void **)&w.status_host, sizeof(int) * ST_WORDS) != cudaSuccess)

@@ -99,7 +99,9 @@ struct elsi_gb_handle_s {
     bool have_cedm = false;
     // several independent problems (k-points / spin channels): batch.cu
     egb::BatchState *batch = nullptr;
-    int batch_workers = 0;  // concurrent solves of a batch (0: by problem size)
+    int batch_workers = 0;  // concurrent solves of a batch (0: chosen by the autotuner)
+    int batch_autotune = 1; // tune band width, tridiagonalisation and concurrency per size
+    bool band_set = false, solver_set = false;  // set explicitly: the autotuner keeps them
     // singularity check of the overlap (sec. 4.4): sing.cu. sing_mode 0 = off, 1 = check,
     // 2 = always transform by the eigendecomposition of S
     int sing_mode = 0;
@@ -138,6 +140,7 @@ int solve_complex(elsi_gb_handle_s *h, const double *ham, const double *ovlp, do
 int get_edm_complex(elsi_gb_handle_s *h, double *edm);
 void free_complex(elsi_gb_handle_s *h);
 void free_batch(elsi_gb_handle_s *h);
+bool batch_tuning_lookup(elsi_gb_handle_s *h, int n, bool cplx, int *band, int *solver, int *workers);
 int dm_adjoint(elsi_gb_handle_s *h, int n, double fb, const double *p, const double *w,
                double *hb, double *sb);
 int ev_adjoint(elsi_gb_handle_s *h, int n, int k, const double *eps, const double *c,

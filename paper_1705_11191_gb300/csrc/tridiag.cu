@@ -8,7 +8,13 @@
 //    O(eps ||T||) in O(n) work; one thread per vector;
 //  * vectors of eigenvalues closer than 1e-5 ||T|| are re-orthogonalised (two passes of
 //    Gram-Schmidt within the cluster, as in inverse-iteration codes), which bounds the
-//    loss of orthogonality between any two returned vectors by about eps*1e5.
+//    loss of orthogonality between close vectors by about eps*1e5. A cluster is worked
+//    on in pieces of 64 consecutive vectors and then in the 64-vector seams across piece
+//    boundaries, so that a long chain of close eigenvalues (an ill-conditioned overlap
+//    puts one huge eigenvalue into ||T|| and with it every gap of the rest of the
+//    spectrum below the threshold) costs O(64 n) per vector instead of O(cluster n):
+//    vectors more than 32 places apart are left as the twisted factorisation gives them,
+//    orthogonal to about eps ||T|| / (32 times the eigenvalue spacing).
 // All of this runs in binary64 regardless of the precision of the reduction.
 #include <float.h>
 
@@ -139,7 +145,10 @@ __global__ void bisect_kernel(int n, const double *d, const double *e, int count
     }
     if (active) {
         for (int it = 0; it < 128; ++it) {
-            double tol = fmax(tol_rel * tn, 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))) + 4.0 * pivmin;
+            // tol_rel relative to ||T||, but not looser than 10 tol_rel |lambda| (a single
+            // huge eigenvalue of an ill-conditioned overlap must not loosen all others)
+            const double scale = fmin(tn, 10.0 * fmax(1.0, fmax(fabs(lo), fabs(hi))));
+            double tol = fmax(tol_rel * scale, 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))) + 4.0 * pivmin;
             if (hi - lo <= tol) break;
             double sig = lo + (hi - lo) * (double)(lane + 1) / (double)(LANES + 1);
             int c = sturm_count(n, d, e, sig, pivmin);
@@ -342,8 +351,40 @@ __device__ __forceinline__ double hash_unit(unsigned a, unsigned b)
     return (double)h * (2.0 / 4294967296.0) - 1.0;
 }
 
-// One CTA per cluster start: Gram-Schmidt (two passes) within clusters of eigenvalues
-// closer than tol_rel * ||T||. A vector that the projection nearly annihilates (its
+constexpr int kOrthPiece = 64;  // vectors orthogonalised together (pieces and seams)
+
+// cstart[i] = first index of the cluster of i (chains of eigenvalues closer than
+// tol_rel * ||T||). One CTA: each thread scans a contiguous segment, then the segment
+// results are combined in order.
+__global__ void cluster_start_kernel(int kvec, const double *w, const double *bounds, double tol_rel,
+                                     int *cstart)
+{
+    __shared__ int last[1024];
+    const double tol = tol_rel * fmax(bounds[3], DBL_MIN);
+    const int nt = blockDim.x, t = threadIdx.x;
+    const int seg = (kvec + nt - 1) / nt;
+    const int a = t * seg, b = min(kvec, a + seg);
+    int cur = -1;  // start of the current cluster inside the segment (-1: continues from left)
+    for (int i = a; i < b; ++i) {
+        if (i == 0 || !(w[i] - w[i - 1] < tol)) cur = i;
+        cstart[i] = cur;
+    }
+    last[t] = cur;
+    __syncthreads();
+    if (t == 0)
+        for (int q = 1; q < nt; ++q)
+            if (last[q] < 0) last[q] = last[q - 1];
+    __syncthreads();
+    if (a < b && t > 0) {
+        const int carry = last[t - 1];
+        for (int i = a; i < b && cstart[i] < 0; ++i) cstart[i] = carry;
+    }
+}
+
+// Gram-Schmidt (two passes) within clusters of eigenvalues closer than tol_rel * ||T||,
+// on ranges of at most kOrthPiece vectors: phase 0 takes the pieces [s + 64p, s + 64p + 64)
+// of a cluster starting at s, phase 1 the seams [s + 64p + 32, s + 64p + 96) that cross a
+// piece boundary; one CTA per range start. A vector that the projection nearly annihilates (its
 // eigenvalue coincides with an earlier one to working accuracy, as for the pairs of the
 // real form of a complex Hermitian matrix) is replaced by one step of inverse iteration
 // on its block, x = (T_b - lambda I)^{-1} b for a pseudo-random b orthogonal to the
@@ -353,16 +394,19 @@ __device__ __forceinline__ double hash_unit(unsigned a, unsigned b)
 // eigenvalue than to its own, that vector dominates x; what is left after the projection
 // is still accurate as long as it is far above the rounding level.
 template <typename T>
-__global__ void cluster_orth_kernel(int n, int kvec, const double *w, const double *e,
-                                    const double *bounds, const int *blk, double tol_rel,
-                                    const double *dplus, double *work, T *z, int ldz, int *status)
+__global__ void cluster_orth_kernel(int n, int kvec, const int *cstart, int phase, const double *e,
+                                    const int *blk, const double *dplus, double *work, T *z, int ldz,
+                                    int *status)
 {
     __shared__ double red[32];
     const int i0 = blockIdx.x;
-    const double tol = tol_rel * fmax(bounds[3], DBL_MIN);
-    if (i0 > 0 && w[i0] - w[i0 - 1] < tol) return;  // not a cluster start
-    int i1 = i0 + 1;
-    while (i1 < kvec && w[i1] - w[i1 - 1] < tol) ++i1;
+    const int s = cstart[i0];
+    const int off = phase == 0 ? 0 : kOrthPiece / 2;
+    if ((i0 - s) % kOrthPiece != off) return;  // not a range start
+    int cend = i0 + 1;  // end of the cluster, looked for up to the end of the range
+    while (cend < kvec && cend < i0 + kOrthPiece && cstart[cend] == s) ++cend;
+    if (phase == 1 && cend <= i0 + kOrthPiece / 2) return;  // no piece boundary inside
+    const int i1 = cend;
     if (i1 - i0 < 2) return;
     for (int v = i0 + 1; v < i1; ++v) {
         T *zv = z + (size_t)v * ldz;
@@ -447,9 +491,15 @@ cudaError_t stein(cudaStream_t st, int n, const double *d, const double *e, int 
     EGB_COUNT_LAUNCH();
     twisted_kernel<T><<<ceil_div(kvec, 64), 64, 0, st>>>(n, d, e, kvec, w, bounds, blk, z, ldz, dplus,
                                                         uminus, lplus, status);
+    // cluster starts (in the L+ scratch, no longer needed), then pieces and seams
+    int *cstart = reinterpret_cast<int *>(lplus);
     EGB_COUNT_LAUNCH();
-    cluster_orth_kernel<T><<<kvec, 256, 0, st>>>(n, kvec, w, e, bounds, blk, 1e-5, dplus, uminus,
-                                                 z, ldz, status);
+    cluster_start_kernel<<<1, 1024, 0, st>>>(kvec, w, bounds, 1e-5, cstart);
+    for (int phase = 0; phase < 2; ++phase) {
+        EGB_COUNT_LAUNCH();
+        cluster_orth_kernel<T><<<kvec, 256, 0, st>>>(n, kvec, cstart, phase, e, blk, dplus, uminus, z,
+                                                     ldz, status);
+    }
     return cudaGetLastError();
 }
 

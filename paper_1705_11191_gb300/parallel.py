@@ -15,7 +15,8 @@ tensors, gloo for CPU tensors).
 """
 from __future__ import annotations
 
-__all__ = ["partition", "allgather_varlen", "dm_batched_distributed"]
+__all__ = ["partition", "max_states_per_rank", "allgather_varlen", "allgather_levels",
+           "dm_batched_distributed"]
 
 
 def partition(sizes, world_size: int):
@@ -33,6 +34,34 @@ def partition(sizes, world_size: int):
         parts[r].append(i)
         load[r] += float(sizes[i]) ** 3
     return [sorted(p) for p in parts]
+
+
+def max_states_per_rank(sizes, n_states, world_size: int) -> int:
+    """Largest number of states any rank holds under partition(sizes, world_size): the
+    padded length of the packed exchange, computable by every rank without communication."""
+    return max([sum(int(n_states[i]) for i in p) for p in partition(sizes, world_size)] + [0])
+
+
+def allgather_levels(eps, wt, max_states: int, group=None):
+    """One all-gather of this rank's eigenvalues and weights packed with their count,
+    [count, eps (max_states), weights (max_states)] in binary64, max_states >= the count of
+    every rank. Returns (all eigenvalues, all weights, per-rank counts), in rank order."""
+    import torch
+    import torch.distributed as dist
+    m = int(eps.numel())
+    if m > max_states:
+        raise ValueError(f"{m} states exceed max_states = {max_states}")
+    ws = dist.get_world_size(group)
+    buf = torch.zeros(1 + 2 * max_states, dtype=torch.float64, device=eps.device)
+    buf[0] = float(m)
+    buf[1: 1 + m] = eps
+    buf[1 + max_states: 1 + max_states + m] = wt
+    bufs = [torch.zeros_like(buf) for _ in range(ws)]
+    dist.all_gather(bufs, buf, group=group)
+    lens = [int(b[0].item()) for b in bufs]
+    eps_all = torch.cat([b[1: 1 + k] for b, k in zip(bufs, lens)])
+    wt_all = torch.cat([b[1 + max_states: 1 + max_states + k] for b, k in zip(bufs, lens)])
+    return eps_all, wt_all, lens
 
 
 def allgather_varlen(t, group=None):
@@ -54,12 +83,14 @@ def allgather_varlen(t, group=None):
 
 
 def dm_batched_distributed(solver, hams, ovlps, n_states, weights, n_electron: float,
-                           group=None, device=None):
+                           group=None, device=None, max_states: int | None = None):
     """This rank's problems (hams, ovlps, n_states, weights: lists over its problems) with
     one chemical potential over the problems of all ranks:
         sum over all ranks' problems i of weights[i] * sum_l f_il = n_electron.
-    A rank without problems takes part in the exchange only (its tensors live on
-    ``device``). Returns (P list, W list, band energies, mu) for this rank's problems."""
+    max_states (max_states_per_rank of the global problem list): the eigenvalues and
+    weights travel in one all-gather; without it the counts are gathered first. A rank
+    without problems takes part in the exchange only (its tensors live on ``device``).
+    Returns (P list, W list, band energies, mu) for this rank's problems."""
     import torch
     import torch.distributed as dist
     if len(hams):
@@ -69,8 +100,13 @@ def dm_batched_distributed(solver, hams, ovlps, n_states, weights, n_electron: f
     else:
         eps = torch.empty(0, dtype=torch.float64, device=device or "cpu")
         wt = eps.clone()
-    eps_all, lens = allgather_varlen(eps, group)
-    wt_all, _ = allgather_varlen(wt, group)
+    if max_states is None:
+        import torch.distributed as dist
+        cnt = torch.tensor([float(eps.numel())], dtype=torch.float64, device=eps.device)
+        cnts = [torch.zeros_like(cnt) for _ in range(dist.get_world_size(group))]
+        dist.all_gather(cnts, cnt, group=group)
+        max_states = int(max(float(c.item()) for c in cnts))
+    eps_all, wt_all, lens = allgather_levels(eps, wt, max_states, group)
     f_all, mu = solver.occupation_weighted(eps_all, wt_all, n_electron)
     r = dist.get_rank(group)
     off = sum(lens[:r])

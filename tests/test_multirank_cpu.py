@@ -60,7 +60,7 @@ class OracleSolver:
         return P, W, en
 
 
-def _rank_main(rank, world, port, outdir, scheme, kt, n_el):
+def _rank_main(rank, world, port, outdir, scheme, kt, n_el, packed=True):
     import torch.distributed as dist
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
                             world_size=world)
@@ -68,10 +68,12 @@ def _rank_main(rank, world, port, outdir, scheme, kt, n_el):
         mine = parallel.partition(SIZES, world)[rank]
         probs = [_problem(i) for i in mine]
         ks = [p.n // 2 for p in probs]
+        # one all-gather: the padded length comes from the global problem list
+        mx = parallel.max_states_per_rank(SIZES, [n // 2 for n in SIZES], world) if packed else None
         P, W, en, mu = parallel.dm_batched_distributed(
             OracleSolver(scheme, kt), [torch.from_numpy(np.ascontiguousarray(p.h)) for p in probs],
             [torch.from_numpy(np.ascontiguousarray(p.s)) for p in probs], ks,
-            [WEIGHTS[i] for i in mine], n_el)
+            [WEIGHTS[i] for i in mine], n_el, max_states=mx)
         for j, i in enumerate(mine):
             np.save(os.path.join(outdir, f"P{i}.npy"), P[j].numpy())
             np.save(os.path.join(outdir, f"W{i}.npy"), W[j].numpy())
@@ -100,13 +102,14 @@ def test_partition_covers_and_balances():
     assert parallel.partition([10], 3) == [[0], [], []]
 
 
-@pytest.mark.parametrize("scheme,kt,n_el", [(2, 0.01, 9.0), (0, 0.0, 10.0)])
-def test_two_rank_shared_mu_matches_single_process(scheme, kt, n_el):
+@pytest.mark.parametrize("scheme,kt,n_el,packed", [(2, 0.01, 9.0, True), (0, 0.0, 10.0, True),
+                                                   (2, 0.01, 9.0, False)])
+def test_two_rank_shared_mu_matches_single_process(scheme, kt, n_el, packed):
     import torch.multiprocessing as tmp
     import oracle
     with tempfile.TemporaryDirectory() as outdir:
         port = _free_port()
-        tmp.spawn(_rank_main, args=(2, port, outdir, scheme, kt, n_el), nprocs=2, join=True)
+        tmp.spawn(_rank_main, args=(2, port, outdir, scheme, kt, n_el, packed), nprocs=2, join=True)
         probs = [_problem(i) for i in range(len(SIZES))]
         ref, ref_mu = oracle.solve_batched([(p.h, p.s, p.n // 2) for p in probs], n_el,
                                            weights=WEIGHTS, scheme=scheme, kt=kt)

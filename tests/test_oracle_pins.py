@@ -324,3 +324,19 @@ def test_complex_kpoint_invariants():
     e = r["energy"]
     assert abs(np.trace(P @ H).real - e) < 1e-10 * abs(e)
     assert abs(np.trace(W @ S).real - e) < 1e-10 * abs(e)
+
+
+def test_batch_generators_match_the_single_problem_recipe():
+    """The batch generators (torch construction, used for the k-point and mixed-size
+    batches) reproduce the numpy recipe of the single-problem generators."""
+    torch = pytest.importorskip("torch")
+    p = ksinputs.cluster_problem(150, seed=1007)
+    h, s, ne, ns, lam = ksinputs.cluster_problem_torch(150, 1007, "cpu")
+    assert np.abs(h.numpy() - p.h).max() < 1e-15 and np.abs(s.numpy() - p.s).max() < 1e-15
+    assert (ne, ns) == (p.n_electron, p.n_state) and abs(lam - p.lambda_min_s) < 1e-12
+    for kf, hk, sk, lk in ksinputs.kpoint_set(30, grid=2, seed=8)[::3]:
+        q = ksinputs.kpoint_problem(30, kf, seed=8)
+        assert np.abs(hk.numpy() - q.h).max() < 1e-15 and np.abs(sk.numpy() - q.s).max() < 1e-15
+        assert abs(lk - q.lambda_min_s) < 1e-12
+    sizes = ksinputs.mixed_sizes()
+    assert len(sizes) == 200 and min(sizes) >= 256 and max(sizes) <= 4096
