@@ -44,6 +44,11 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the several-problem workloads (k-point batch, mixed sizes)")
     ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--fd-check", type=int, default=0, metavar="N",
+                    help="instead of the benchmark: the free-energy derivative check at size N "
+                         "(binary32 + refinement forward, Fermi-Dirac kT = 0.01, dF/dH = P and "
+                         "dF/dS = -W against central differences on random symmetric directions)")
+    ap.add_argument("--fd-dirs", type=int, default=32)
     ap.add_argument("--lambda-min", type=float, default=None,
                     help="force lambda_min(S) to this value (the overlap-conditioning sweep)")
     return ap.parse_args()
@@ -197,6 +202,10 @@ def main():
     import paper_1705_11191_gb300 as egb
 
     torch.cuda.set_device(local)
+    if args.fd_check:
+        if rank == 0:
+            print(json.dumps(fd_check(egb, torch, args.fd_check, args.fd_dirs)), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -328,6 +337,75 @@ def main():
     hd.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def fd_check(egb, torch, n: int, ndirs: int, h: float = 1e-6, kt: float = 0.01) -> dict:
+    """Derivatives of the Mermin free energy F = E_band - kT S_ent of the 3D-cluster problem
+    of size n (seed 5, N_el = n/4), binary32 + refinement forward, Fermi-Dirac kT = 0.01 Ha,
+    mu bisected to |N(mu) - N_el| <= 1e-12, n_state = N_el/2 + n/10 (enough states that the
+    occupation of the first unused one is below 1e-15). The backward gives dF/dH = P and
+    dF/dS = -W (elsi_dm_adjoint_real through KSFreeEnergy). Each of ndirs random symmetric
+    directions D (entries N(0,1), seed 6) is checked by central differences:
+    (F(H + hD) - F(H - hD)) / 2h against <dF/dH, D>, and likewise for S (S +- hD)."""
+    import ksinputs
+    from paper_1705_11191_gb300 import autograd as ega
+    dev = torch.device("cuda")
+    t0 = time.perf_counter()
+    H, S, nel, _, lam = ksinputs.cluster_problem_torch(n, 5, dev)
+    nstate = min(n, int(nel // 2 + n // 10))
+    gen_s = time.perf_counter() - t0
+    hd = egb.Handle(n, nstate, nel)
+    hd.use_current_stream()
+    hd.set_precision(egb.PREC_FP32_REFINE)
+    hd.set_broadening(egb.OCC_FERMI, kt)
+    hd.set_occ_accuracy(1e-12)
+    Hr = H.clone().requires_grad_(True)
+    Sr = S.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    F = ega.free_energy(Hr, Sr, hd)
+    torch.cuda.synchronize()
+    fwd_s = time.perf_counter() - t1
+    iters, orth = hd.refine_info()
+    occ = hd.get_occ()
+    t2 = time.perf_counter()
+    F.backward()
+    torch.cuda.synchronize()
+    bwd_s = time.perf_counter() - t2
+    gH, gS = Hr.grad, Sr.grad
+    del Hr, Sr
+    F0 = float(F)
+    gen = torch.Generator(device=dev).manual_seed(6)
+    rows = []
+
+    def energy(Hx, Sx):
+        P, e = hd.dm_real(Hx, Sx)
+        del P
+        return e + hd.get_entropy()
+
+    for q in range(ndirs):
+        D = torch.randn((n, n), dtype=torch.float64, device=dev, generator=gen)
+        D = 0.5 * (D + D.T)
+        for which in ("H", "S"):
+            g = gH if which == "H" else gS
+            an = float((g * D).sum())
+            if which == "H":
+                fp, fm = energy(H + h * D, S), energy(H - h * D, S)
+            else:
+                fp, fm = energy(H, S + h * D), energy(H, S - h * D)
+            fd = (fp - fm) / (2.0 * h)
+            rows.append({"dir": q, "wrt": which, "analytic": an, "central_difference": fd,
+                         "rel_err": abs(fd - an) / max(abs(an), 1e-300)})
+        del D
+    hd.close()
+    errs = [r["rel_err"] for r in rows]
+    return {"check": "free-energy derivatives by central differences", "n": n,
+            "n_electron": nel, "n_state": nstate, "kT": kt, "lambda_min_s": lam,
+            "occ_of_last_state": float(occ[-1]), "F": F0, "refine_iters": iters,
+            "orth_err": orth, "forward_s": fwd_s, "backward_s": bwd_s,
+            "input_generation_s": gen_s, "step": h, "directions": ndirs,
+            "max_rel_err": max(errs) if errs else None,
+            "median_rel_err": sorted(errs)[len(errs) // 2] if errs else None, "rows": rows}
 
 
 def _bucket(n: int) -> int:

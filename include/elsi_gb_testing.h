@@ -34,6 +34,21 @@ extern "C" {
 int elsi_gb_set_spin_limit(long long polls);
 long long elsi_gb_get_spin_limit(void);
 
+/*
+ * elsi_gb_q2_apply_f32: the binary32 back-transformation through Q2 of the band-to-
+ *   tridiagonal reduction (step (4) of the two-stage method, sec. 3.1), Z <- Q2 Z, on the
+ *   tcgen05 tensor cores. v2: device float[(n-2) * S * b], S = (n-2)/b + 1, the Householder
+ *   vector of bulge-chase step t of sweep j at v2[(j*S + t)*b ...] (v[0] = 1, acting on rows
+ *   j+1+t*b .. j+t*b+b, entries beyond row n-1 zero); tau2: device float[(n-2) * S];
+ *   Z: device n x k column-major, ld ldz >= n; b a multiple of 8 in 8..64. work: device
+ *   scratch of elsi_gb_q2_work(n, b) floats (16-byte aligned); status: device int[8], zeroed
+ *   by the caller (ELSI_ERR_TIMEOUT if a bounded wait expired). Enqueued on stream (may be
+ *   NULL). Returns 0, ELSI_ERR_ARG, ELSI_ERR_CUDA.
+ */
+size_t elsi_gb_q2_work(int n, int b);
+int elsi_gb_q2_apply_f32(int n, int b, const float *v2, const float *tau2, int k, float *z, int ldz,
+                         float *work, size_t work_elems, int *status, void *stream);
+
 size_t elsi_gb_gemm_f32_work(int m, int n, int k);
 int elsi_gb_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const float *A, int lda,
                      const float *B, int ldb, float beta, float *C, int ldc, int uplo,

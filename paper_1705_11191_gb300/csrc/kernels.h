@@ -126,9 +126,6 @@ cudaError_t apply_q2(cudaStream_t st, int n, int b, const T *v2, const T *tau2, 
 size_t q2_factor_elems(int n, int b);
 cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const float *tau2, int k,
                         float *z, int ldz, float *fac, int *status);
-size_t q2_tfactor_elems_legacy(int n, int b);
-cudaError_t apply_q2_tc_legacy(cudaStream_t st, int n, int b, const float *v2, const float *tau2, int k,
-                               float *z, int ldz, float *tfac);
 // Z <- Q1 Z in groups of kQ1Group panels; work: q1_work_elems(b, k) elements.
 constexpr int kQ1Group = 4;
 inline size_t q1_work_elems(int b, int k)

@@ -531,21 +531,14 @@ cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const fl
 
 }  // namespace egb
 
-extern "C" size_t elsi_gb_q2_work(int n, int b)
-{
-    const size_t a = egb::q2_factor_elems(n, b), l = egb::q2_tfactor_elems_legacy(n, b);
-    return (a > l ? a : l) + 64;
-}
+extern "C" size_t elsi_gb_q2_work(int n, int b) { return egb::q2_factor_elems(n, b) + 64; }
 
 extern "C" int elsi_gb_q2_apply_f32(int n, int b, const float *v2, const float *tau2, int k, float *z,
-                                    int ldz, float *work, size_t work_elems, int *status, void *stream,
-                                    int variant)
+                                    int ldz, float *work, size_t work_elems, int *status, void *stream)
 {
     if (n < 1 || k < 0 || ldz < n || !v2 || !tau2 || !z || !work || !status) return ELSI_ERR_ARG;
     if (b < 8 || b > 64 || (b & 7) || work_elems < elsi_gb_q2_work(n, b) - 64) return ELSI_ERR_ARG;
-    cudaError_t e = variant == 1
-                        ? egb::apply_q2_tc_legacy((cudaStream_t)stream, n, b, v2, tau2, k, z, ldz, work)
-                        : egb::apply_q2_tc((cudaStream_t)stream, n, b, v2, tau2, k, z, ldz, work, status);
+    cudaError_t e = egb::apply_q2_tc((cudaStream_t)stream, n, b, v2, tau2, k, z, ldz, work, status);
     if (e == cudaErrorInvalidValue) return ELSI_ERR_ARG;
     return e == cudaSuccess ? ELSI_OK : ELSI_ERR_CUDA;
 }

@@ -374,10 +374,14 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
         // products on the tensor cores; the factor and the inverses of its diagonal blocks
         // are then rounded to binary32 for the standard form and the back-substitution.
         CKR(check_finite<double>(st, n, n, rq.ovlp, n, w.status));
-        double *L64 = w.v1;                                        // n x n, free until full->band
-        double *INV64 = reinterpret_cast<double *>(w.stein);       // n x kTriBlock
+        // the binary64 factor and the digit planes of its updates in the (still unused)
+        // digit-plane buffer
+        double *L64 = reinterpret_cast<double *>(w.oz);                // n x n
+        double *INV64 = reinterpret_cast<double *>(w.stein);           // n x kTriBlock
+        __nv_bfloat16 *cdig = w.oz + (size_t)4 * n * n;                 // after L64
         CKR(copy_matrix<double, double>(st, n, n, rq.ovlp, n, L64, n));
-        set_f64_tc_scratch(w.oz, w.oz_cap / sizeof(__nv_bfloat16), w.ozexp, w.ozexp_cap / sizeof(int));
+        set_f64_tc_scratch(cdig, w.oz_cap / sizeof(__nv_bfloat16) - (size_t)4 * n * n, w.ozexp,
+                           w.ozexp_cap / sizeof(int));
         cudaError_t pe = potrf<double>(st, n, L64, n, INV64, w.edm, w.status);
         set_f64_tc_scratch(nullptr, 0, nullptr, 0);
         CKR(pe);
@@ -414,7 +418,8 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     // binary32-route eigenvalues: the wanted ones are recomputed by the refinement and the
     // rest are reported at the accuracy of this route, so 1e-10 ||T|| suffices
     CKR(stebz(st, n, w.d, w.e, n, w.w, w.status, 1e-10));
-    CKR(stein<float>(st, n, w.d, w.e, n, w.w, X32, n, w.stein, w.status));
+    // eigenvector scratch (3 n^2 + n binary64 values) in the digit-plane buffer, free here
+    CKR(stein<float>(st, n, w.d, w.e, n, w.w, X32, n, reinterpret_cast<double *>(w.oz), w.status));
     CKR(cudaEventRecord(w.ev[STAGE_Q2], st));
     if (!one_stage) CKR(apply_q2_tc(st, n, b, V2, TAU2, n, X32, n, w.q2f, w.status));
     CKR(cudaEventRecord(w.ev[STAGE_Q1], st));

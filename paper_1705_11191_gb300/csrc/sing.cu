@@ -171,6 +171,9 @@ int solve_singular(elsi_gb_handle_s *h, const SolveRequest &rq)
     int rc = ensure_workspace(h, k);
     if (rc) return rc;
     Workspace &w = h->wk;
+    // scratch of the density-matrix products below: n x k binary64 values
+    if (!ensure_buf((void **)&w.v1, &w.v1_cap, sizeof(double) * (size_t)n * k))
+        return set_error(h, ELSI_ERR_NOMEM, "cannot allocate the density scratch");
     cudaStream_t st = h->stream;
     SCK(cudaMemsetAsync(w.status, 0, sizeof(int) * ST_WORDS, st));
     SENSURE(w1, (size_t)n * nn);

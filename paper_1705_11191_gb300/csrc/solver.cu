@@ -30,6 +30,11 @@ void free_workspace(elsi_gb_handle_s *h)
         return set_error(h, ELSI_ERR_NOMEM, "cannot allocate %s (%zu bytes)", #name,       \
                          sizeof(type) * (size_t)(count));
 
+// Buffers of one solve. In the binary32 route the reduction buffers (a, l, v1, v2, tau2,
+// z) hold binary32 values and are sized for them; the tridiagonal eigenvector scratch and
+// the binary64 Cholesky factor live in the digit-plane buffer oz, which is free at those
+// stages (its planes are formed after the back-transformations). A binary64 fallback of a
+// binary32 solve grows the buffers to binary64 sizes first.
 int ensure_workspace(elsi_gb_handle_s *h, int kz)
 {
     Workspace &w = h->wk;
@@ -37,12 +42,14 @@ int ensure_workspace(elsi_gb_handle_s *h, int kz)
     const int b = h->band_width;
     const int S = sb2st_steps(h->n, b);
     const size_t nsweep = n >= 3 ? n - 2 : 1;
-    ENSURE(a, double, n * n);
-    ENSURE(l, double, n * n);
-    ENSURE(v1, double, n * n);
+    const bool fp32 = h->precision == ELSI_PREC_FP32_REFINE;
+    const size_t eb = fp32 ? sizeof(float) : sizeof(double);  // reduction element size
+    ENSURE(a, char, n * n * eb);
+    ENSURE(l, char, n * n * eb);
+    ENSURE(v1, char, n * n * eb);
     ENSURE(edm, double, n * n);
-    ENSURE(v2, double, nsweep * S * b);
-    ENSURE(tau2, double, nsweep * S);
+    ENSURE(v2, char, nsweep * S * b * eb);
+    ENSURE(tau2, char, nsweep * S * eb);
     ENSURE(band, double, (2 * b + 1) * n);
     ENSURE(t1, double, (size_t)(b > kOneStageNb ? b : kOneStageNb) * n);
     ENSURE(invd, double, n * kTriBlock);
@@ -54,13 +61,17 @@ int ensure_workspace(elsi_gb_handle_s *h, int kz)
     if (q1_work_elems(b, kz) > work) work = q1_work_elems(b, kz);
     if (h->elpa_solver == 1 && onestage_work_elems(h->n) > work) work = onestage_work_elems(h->n);
     ENSURE(work, double, work + 64);
-    ENSURE(z, double, n * kz);
+    ENSURE(z, char, n * kz * eb);
     ENSURE(d, double, n + 8);
     ENSURE(e, double, n + 8);
     ENSURE(w, double, n + 8);
     ENSURE(f, double, n + 8);
     ENSURE(scal, double, 64);
-    ENSURE(stein, double, 3 * n * kz + kz + 64);
+    if (fp32) {
+        ENSURE(stein, double, n * kTriBlock + 64);  // binary64 diagonal-block inverses
+    } else {
+        ENSURE(stein, double, 3 * n * kz + kz + 64);
+    }
     ENSURE(sync, unsigned, 64 + 2 * (1024 + 64 + 1024 * 64 + 1024 * 64 * 64));
     ENSURE(status, int, ST_WORDS);
     if (h->precision == ELSI_PREC_FP32_REFINE) {
@@ -73,7 +84,9 @@ int ensure_workspace(elsi_gb_handle_s *h, int kz)
                                       3 * ozaki_split_elems((int)n, (int)k));
         ENSURE(ozexp, int, 8 * (n + k + 256));
         ENSURE(q2f, float, q2_factor_elems((int)n, b));
-        ENSURE(tcw, float, tc_gemm_work_elems((int)n, (int)n, (int)n));
+        // the largest binary32 tensor-core products: X E of the refinement (n x k x n) and
+        // A22 V of the full-to-band reduction (n x b x n); the others have K <= 256
+        ENSURE(tcw, float, tc_gemm_work_elems((int)n, (int)(k > 256 ? k : 256), (int)n));
     }
     if (!w.status_host && cudaMallocHost((void **)&w.status_host, sizeof(int) * ST_WORDS) != cudaSuccess)
         return set_error(h, ELSI_ERR_NOMEM, "pinned status");
@@ -226,6 +239,10 @@ int run_solve(elsi_gb_handle_s *h, const SolveRequest &rq)
             if (nf && nf[0] == '1') return rc;
             CK(cudaMemsetAsync(w.status, 0, sizeof(int) * ST_WORDS, st));
             h->have_l = false;
+            h->precision = ELSI_PREC_FP64;  // binary64 sizes of the reduction buffers
+            rc = ensure_workspace(h, h->n_state);
+            h->precision = ELSI_PREC_FP32_REFINE;
+            if (rc) return rc;
             rc = solve_fp64(h, rq);
             h->refine_iters = -1;
         }

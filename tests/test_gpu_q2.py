@@ -6,7 +6,13 @@ has v[0] = 1 and acts on rows j+1+tb .. j+tb+b (cut at row n-1), tau = 2 / v^T v
 H = I - tau v v^T is orthogonal. Q2 is their product in the order the sequential chase
 generates them (sweep 0 steps 0, 1, ..., then sweep 1, ...), so Z <- Q2 Z applies them in
 the reverse order. Sizes: n not a multiple of 64 or 8, k not a multiple of 128 (ragged
-column tile), all supported band widths kinds (8, 40, 64)."""
+column tile), band widths 8, 40, 64.
+
+The reference applies the reflectors as the kernel receives them (rounded to binary32),
+in binary64, so the comparison measures the kernel's arithmetic alone: binary32 values
+carried through about 2n/64 group applications per element (each a product of the group's
+TF32 hi/lo splits, about binary32 accuracy) leave a relative error of a few 1e-6 at
+n ~ 1000; the bound is 2e-5."""
 import ctypes
 
 import numpy as np
@@ -24,7 +30,7 @@ def _lib():
     lib.elsi_gb_q2_work.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.elsi_gb_q2_work.restype = ctypes.c_size_t
     lib.elsi_gb_q2_apply_f32.argtypes = [ctypes.c_int, ctypes.c_int, v, v, ctypes.c_int, v,
-                                         ctypes.c_int, v, ctypes.c_size_t, v, v, ctypes.c_int]
+                                         ctypes.c_int, v, ctypes.c_size_t, v, v]
     lib.elsi_gb_q2_apply_f32.restype = ctypes.c_int
     return lib
 
@@ -68,21 +74,20 @@ def test_q2_tensor_core_matches_binary64(n, b, k, seed):
     v2, tau, S = _reflectors(n, b, seed)
     rng = np.random.default_rng(100 + seed)
     z0 = rng.standard_normal((n, k))
-    ref = _apply_ref(n, b, v2, tau, S, z0)
-    dv2 = torch.from_numpy(v2.astype(np.float32)).cuda().contiguous()
-    dtau = torch.from_numpy(tau.astype(np.float32)).cuda()
-    errs = {}
-    for variant in (0, 1):
-        zt = torch.from_numpy(np.asfortranarray(z0.astype(np.float32)).T.copy()).cuda()  # (k, n)
-        work = torch.zeros(lib.elsi_gb_q2_work(n, b) + 16, dtype=torch.float32, device="cuda")
-        st = torch.zeros(8, dtype=torch.int32, device="cuda")
-        rc = lib.elsi_gb_q2_apply_f32(n, b, dv2.data_ptr(), dtau.data_ptr(), k, zt.data_ptr(), n,
-                                      work.data_ptr(), work.numel(), st.data_ptr(),
-                                      torch.cuda.current_stream().cuda_stream, variant)
-        torch.cuda.synchronize()
-        assert rc == 0
-        assert int(st[0]) == 0
-        out = zt.cpu().numpy().T.astype(np.float64)
-        errs[variant] = float(np.linalg.norm(out - ref) / np.linalg.norm(ref))
-    print(f"n={n} b={b} k={k}: rel err tcgen05 {errs[0]:.2e}, mma.sync {errs[1]:.2e}")
-    assert errs[0] < 2e-6
+    v32, t32, z32 = v2.astype(np.float32), tau.astype(np.float32), z0.astype(np.float32)
+    ref = _apply_ref(n, b, v32.astype(np.float64), t32.astype(np.float64), S, z32.astype(np.float64))
+    dv2 = torch.from_numpy(v32).cuda().contiguous()
+    dtau = torch.from_numpy(t32).cuda()
+    zt = torch.from_numpy(np.asfortranarray(z32).T.copy()).cuda()  # (k, n) = n x k column-major
+    work = torch.zeros(lib.elsi_gb_q2_work(n, b) + 16, dtype=torch.float32, device="cuda")
+    st = torch.zeros(8, dtype=torch.int32, device="cuda")
+    rc = lib.elsi_gb_q2_apply_f32(n, b, dv2.data_ptr(), dtau.data_ptr(), k, zt.data_ptr(), n,
+                                  work.data_ptr(), work.numel(), st.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert int(st[0]) == 0
+    out = zt.cpu().numpy().T.astype(np.float64)
+    err = float(np.linalg.norm(out - ref) / np.linalg.norm(ref))
+    print(f"n={n} b={b} k={k}: relative error {err:.2e}")
+    assert err < 2e-5
