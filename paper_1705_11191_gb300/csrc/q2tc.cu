@@ -235,6 +235,34 @@ __device__ __forceinline__ void tmem_ld8(unsigned taddr, float *v)
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Eight consecutive rows r0 .. r0+7 of a column (rows >= n read as 0 / not stored); two
+// 16-byte accesses when the column start allows it (vec: ld a multiple of 4) and the eight
+// rows exist, since r0 is a multiple of 8.
+__device__ __forceinline__ void load8(const float *zc, int r0, int n, bool ok, bool vec, float *v)
+{
+    if (ok && vec && r0 + 8 <= n) {
+        const float4 a = *reinterpret_cast<const float4 *>(zc + r0);
+        const float4 c = *reinterpret_cast<const float4 *>(zc + r0 + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = (ok && r0 + i < n) ? zc[r0 + i] : 0.f;
+    }
+}
+
+__device__ __forceinline__ void store8(float *zc, int r0, int n, bool ok, bool vec, const float *v)
+{
+    if (!ok) return;
+    if (vec && r0 + 8 <= n) {
+        *reinterpret_cast<float4 *>(zc + r0) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(zc + r0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (r0 + i < n) zc[r0 + i] = v[i];
+    }
+}
+
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -262,6 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
     const int gc = blockIdx.x * kCols + quarter * 32 + lane;  // column of Z
     const bool colok = gc < a.k;
     float *zc = a.z + (size_t)(colok ? gc : 0) * (size_t)a.ldz;
+    const bool vec = (a.ldz & 3) == 0 && (((size_t)a.z) & 15) == 0;
 
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) mbar_init(smem_u32(&bars[i]), 1);
@@ -317,11 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int p = (half * 64 + c * 8 - J) & (kWin - 1);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = J + p + i;
-                zr[c * 8 + i] = (colok && r < n) ? zc[r] : 0.f;
-            }
+            load8(zc, J + p, n, colok, vec, zr + c * 8);
         }
         for (int t = 0; t < SJ; ++t) {
             const int w0 = J + t * b;
@@ -331,13 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int p = (half * 64 + c * 8 - w0) & (kWin - 1);
-                    if (p < b) {
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int r = w0 + p + kWin + i;
-                            pre[c * 8 + i] = (colok && r < n) ? zc[r] : 0.f;
-                        }
-                    }
+                    if (p < b) load8(zc, w0 + p + kWin, n, colok, vec, pre + c * 8);
                 }
             }
             // ---- A of MMA 1: Z_w^T (hi, lo) at logical window positions
@@ -464,11 +483,10 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
             for (int c = 0; c < 8; ++c) {
                 const int p = (half * 64 + c * 8 - w0) & (kWin - 1);
                 if (last || p < b) {
+                    store8(zc, w0 + p, n, colok, vec, zr + c * 8);
+                    if (!last) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int r = w0 + p + i;
-                        if (colok && r < n) zc[r] = zr[c * 8 + i];
-                        if (!last) zr[c * 8 + i] = pre[c * 8 + i];
+                        for (int i = 0; i < 8; ++i) zr[c * 8 + i] = pre[c * 8 + i];
                     }
                 }
             }

@@ -368,25 +368,32 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
 
     CKR(cudaEventRecord(w.ev[STAGE_CHOL], st));
     if (!unit && !(h->reuse_l && h->have_l && h->have_l_prec == ELSI_PREC_FP32_REFINE)) {
-        // Eq. 8 in binary64: the overlap may be ill-conditioned, and a factor that is accurate
-        // in binary64 keeps the binary32 stages' start as good as binary32 allows. The
-        // trailing updates of the blocked factorisation run as binary64-accurate digit
-        // products on the tensor cores; the factor and the inverses of its diagonal blocks
-        // are then rounded to binary32 for the standard form and the back-substitution.
+        // Eq. 8 in binary32: the factor only feeds the binary32 standard form and
+        // back-substitution, where a binary64 factor rounded to binary32 has the same
+        // backward error (about eps_32 ||S||); the refinement works with S itself.
         CKR(check_finite<double>(st, n, n, rq.ovlp, n, w.status));
-        // the binary64 factor and the digit planes of its updates in the (still unused)
-        // digit-plane buffer
-        double *L64 = reinterpret_cast<double *>(w.oz);                // n x n
-        double *INV64 = reinterpret_cast<double *>(w.stein);           // n x kTriBlock
-        __nv_bfloat16 *cdig = w.oz + (size_t)4 * n * n;                 // after L64
-        CKR(copy_matrix<double, double>(st, n, n, rq.ovlp, n, L64, n));
-        set_f64_tc_scratch(cdig, w.oz_cap / sizeof(__nv_bfloat16) - (size_t)4 * n * n, w.ozexp,
-                           w.ozexp_cap / sizeof(int));
-        cudaError_t pe = potrf<double>(st, n, L64, n, INV64, w.edm, w.status);
-        set_f64_tc_scratch(nullptr, 0, nullptr, 0);
-        CKR(pe);
-        CKR(copy_matrix<float, double>(st, n, n, L64, n, L, n));
-        CKR(copy_matrix<float, double>(st, n, kTriBlock, INV64, n, INVD, n));
+        CKR(copy_matrix<float, double>(st, n, n, rq.ovlp, n, L, n));
+        CKR(potrf<float>(st, n, L, n, INVD, WORK, w.status));
+        CKR(cudaMemcpyAsync(w.status_host, w.status, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, st));
+        CKR(cudaStreamSynchronize(st));
+        if (w.status_host[ST_CODE] == ELSI_ERR_NOT_PD) {
+            // S is positive definite in binary64 but not in binary32 (lambda_min(S) near or
+            // below eps_32 ||S||): factor in binary64, with the trailing and panel updates as
+            // binary64-accurate digit products on the tensor cores (binary64 FMAs are scarce
+            // on this chip), and round the factor and its diagonal-block inverses.
+            CKR(cudaMemsetAsync(w.status, 0, sizeof(int) * ST_WORDS, st));
+            double *L64 = reinterpret_cast<double *>(w.oz);            // n x n, oz unused yet
+            double *INV64 = reinterpret_cast<double *>(w.stein);       // n x kTriBlock
+            __nv_bfloat16 *cdig = w.oz + (size_t)4 * n * n;             // after L64
+            CKR(copy_matrix<double, double>(st, n, n, rq.ovlp, n, L64, n));
+            set_f64_tc_scratch(cdig, w.oz_cap / sizeof(__nv_bfloat16) - (size_t)4 * n * n, w.ozexp,
+                               w.ozexp_cap / sizeof(int));
+            cudaError_t pe = potrf<double>(st, n, L64, n, INV64, w.edm, w.status);
+            set_f64_tc_scratch(nullptr, 0, nullptr, 0);
+            CKR(pe);
+            CKR(copy_matrix<float, double>(st, n, n, L64, n, L, n));
+            CKR(copy_matrix<float, double>(st, n, kTriBlock, INV64, n, INVD, n));
+        }
         h->have_l_prec = ELSI_PREC_FP32_REFINE;
     }
     CKR(cudaEventRecord(w.ev[STAGE_STDFORM], st));
