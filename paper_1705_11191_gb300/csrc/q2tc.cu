@@ -28,9 +28,9 @@
 // each group's products start from fresh accumulators, so tensor-memory accumulation never
 // sums more than 3 x K/8 partial products into one value.
 //
-// CTA (256 threads, 8 warps, one CTA per SM): 128 columns of Z; warp w owns the columns
+// CTA (512 threads, 16 warps, one CTA per SM): 128 columns of Z; warp w owns the columns
 // 32 (w mod 4) .. +31 (one per lane, the tensor-memory lane quarter of the warp) and the
-// window slots 64 (w / 4) .. +63 of them, in registers. The A operands (Z_w^T, then Y^T,
+// window slots 32 (w / 4) .. +31 of them, in registers. The A operands (Z_w^T, then Y^T,
 // hi and lo) are written to tensor memory with tcgen05.st; V and W (hi and lo) come from a
 // per-group block that the factor kernel writes already in the shared-memory layout of the
 // B operand (K-major, 128-byte swizzle), fetched with bulk asynchronous copies: V of the
@@ -52,7 +52,10 @@ using namespace tc5;
 constexpr int kM = 64;       // reflectors per group (sweeps per block)
 constexpr int kWin = 128;    // window rows
 constexpr int kCols = 128;   // columns of Z per CTA
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;                    // 16 warps
+constexpr int kParts = kThreads / 128;           // warps per tensor-memory lane quarter
+constexpr int kSlots = kWin / kParts;            // window slots per thread (32)
+constexpr int kChunks = kSlots / 8;              // chunks of 8 slots per thread
 constexpr int kVPlane = kWin * kM * 4;  // bytes of one plane of V: 4 K-chunks of [64 a][32 rows]
 constexpr int kWPlane = kWin * kM * 4;  // bytes of one plane of W: 2 K-chunks of [128 rows][32 a]
 constexpr int kGroupBytes = 2 * kVPlane + 2 * kWPlane;  // VH | VL | WH | WL = 128 KB
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
     const unsigned sV = smem_u32(smem), sW = sV + 2 * kVPlane;
     const int n = a.n, b = a.b;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, part = warp >> 2;
     const int gc = blockIdx.x * kCols + quarter * 32 + lane;  // column of Z
     const bool colok = gc < a.k;
     float *zc = a.z + (size_t)(colok ? gc : 0) * (size_t)a.ldz;
@@ -331,8 +334,8 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
         v_out = w_out = true;
     }
 
-    float zr[64];   // slots 64 half + i of this thread's column
-    float pre[64];  // rows entering the window after the current group
+    float zr[kSlots];   // slots kSlots * part + i of this thread's column
+    float pre[kSlots];  // rows entering the window after the current group
     const unsigned idesc1 = idesc_f32acc(2, 128, 64);
     const unsigned idesc2 = idesc_f32acc(2, 128, 128);
     bool ok = true;
@@ -344,8 +347,8 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
         const long long gnext_block = jb > 0 ? gbase - block_steps(n, b, J - kM) : -1;
         // initial window of the block: rows J .. J+127
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int p = (half * 64 + c * 8 - J) & (kWin - 1);
+        for (int c = 0; c < kChunks; ++c) {
+            const int p = (part * kSlots + c * 8 - J) & (kWin - 1);
             load8(zc, J + p, n, colok, vec, zr + c * 8);
         }
         for (int t = 0; t < SJ; ++t) {
@@ -354,15 +357,15 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
             // prefetch the rows that replace the ones leaving after this group
             if (!last) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int p = (half * 64 + c * 8 - w0) & (kWin - 1);
+                for (int c = 0; c < kChunks; ++c) {
+                    const int p = (part * kSlots + c * 8 - w0) & (kWin - 1);
                     if (p < b) load8(zc, w0 + p + kWin, n, colok, vec, pre + c * 8);
                 }
             }
             // ---- A of MMA 1: Z_w^T (hi, lo) at logical window positions
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const unsigned p = (unsigned)((half * 64 + c * 8 - w0) & (kWin - 1));
+            for (int c = 0; c < kChunks; ++c) {
+                const unsigned p = (unsigned)((part * kSlots + c * 8 - w0) & (kWin - 1));
                 unsigned hi[8], lo[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -383,10 +386,12 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
                 } else {
                     v_out = false;
                     tc_fence_after();
-#pragma unroll 1
+                    const unsigned long long dv_h = sdesc(sV), dv_l = sdesc(sV + kVPlane);
+#pragma unroll
                     for (int kk = 0; kk < kWin / 8; ++kk) {
-                        const unsigned boff = (kk >> 2) * (kM * 128) + (kk & 3) * 32;
-                        const unsigned long long bh = sdesc(sV + boff), bl = sdesc(sV + kVPlane + boff);
+                        // the descriptor's start address is in 16-byte units
+                        const unsigned boff = ((kk >> 2) * (kM * 128) + (kk & 3) * 32) >> 4;
+                        const unsigned long long bh = dv_h + boff, bl = dv_l + boff;
                         const unsigned ah = tmem + kZH + kk * 8, al = tmem + kZL + kk * 8;
                         const unsigned acc = kk > 0 ? 1u : 0u;
                         mma_tf32_ts(tmem + kYAccX, al, bh, idesc1, acc);
@@ -410,13 +415,18 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
                 m1_out = false;
                 if (gnext >= 0) { load_v(fac_of(gnext)); v_out = true; }
             }
-            // ---- A of MMA 2: Y^T (hi, lo); warp half h takes a = 32 h .. 32 h + 31
+            // ---- A of MMA 2: Y^T (hi, lo); warp part q takes a = 16 q .. 16 q + 15
             {
-                float yh[32], yx[32];
-                tmem_ld32(tq + kYAccH + 32 * half, yh);
-                tmem_ld32(tq + kYAccX + 32 * half, yx);
+                constexpr int kA = kM / kParts;
+                float yh[kA], yx[kA];
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
+                for (int g = 0; g < kA / 8; ++g) {
+                    tmem_ld8(tq + kYAccH + kA * part + 8 * g, yh + 8 * g);
+                    tmem_ld8(tq + kYAccX + kA * part + 8 * g, yx + 8 * g);
+                }
+                tmem_wait_ld();
+#pragma unroll
+                for (int g = 0; g < kA / 8; ++g) {
                     unsigned hi[8], lo[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -424,8 +434,8 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
                         hi[i] = tf32_hi(y);
                         lo[i] = __float_as_uint(y - __uint_as_float(hi[i]));
                     }
-                    tmem_st8(tq + kZH + 32 * half + 8 * g, hi);
-                    tmem_st8(tq + kZL + 32 * half + 8 * g, lo);
+                    tmem_st8(tq + kZH + kA * part + 8 * g, hi);
+                    tmem_st8(tq + kZL + kA * part + 8 * g, lo);
                 }
             }
             tmem_wait_st();
@@ -440,10 +450,11 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
                 } else {
                     w_out = false;
                     tc_fence_after();
-#pragma unroll 1
+                    const unsigned long long dw_h = sdesc(sW), dw_l = sdesc(sW + kWPlane);
+#pragma unroll
                     for (int kk = 0; kk < kM / 8; ++kk) {
-                        const unsigned boff = (kk >> 2) * (kWin * 128) + (kk & 3) * 32;
-                        const unsigned long long bh = sdesc(sW + boff), bl = sdesc(sW + kWPlane + boff);
+                        const unsigned boff = ((kk >> 2) * (kWin * 128) + (kk & 3) * 32) >> 4;
+                        const unsigned long long bh = dw_h + boff, bl = dw_l + boff;
                         const unsigned ah = tmem + kZH + kk * 8, al = tmem + kZL + kk * 8;
                         const unsigned acc = kk > 0 ? 1u : 0u;
                         mma_tf32_ts(tmem + kAccX, al, bh, idesc2, acc);
@@ -465,23 +476,25 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
                 m2_out = false;
                 if (gnext >= 0) { load_w(fac_of(gnext)); w_out = true; }
             }
-            // ---- Z_w += dZ
+            // ---- Z_w += dZ (all loads of the thread in flight together)
+            {
+                float dh[kSlots], dx[kSlots];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const unsigned p = (unsigned)((half * 64 + c * 8 - w0) & (kWin - 1));
-                float dh[8], dx[8];
-                tmem_ld8(tq + kAccH + p, dh);
-                tmem_ld8(tq + kAccX + p, dx);
+                for (int c = 0; c < kChunks; ++c) {
+                    const unsigned p = (unsigned)((part * kSlots + c * 8 - w0) & (kWin - 1));
+                    tmem_ld8(tq + kAccH + p, dh + 8 * c);
+                    tmem_ld8(tq + kAccX + p, dx + 8 * c);
+                }
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 8; ++i) zr[c * 8 + i] += dh[i] + dx[i];
+                for (int i = 0; i < kSlots; ++i) zr[i] += dh[i] + dx[i];
             }
             tc_fence_before();
             ++gidx;
             // ---- rows leaving the window: store, and take the prefetched rows in their slots
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int p = (half * 64 + c * 8 - w0) & (kWin - 1);
+            for (int c = 0; c < kChunks; ++c) {
+                const int p = (part * kSlots + c * 8 - w0) & (kWin - 1);
                 if (last || p < b) {
                     store8(zc, w0 + p, n, colok, vec, zr + c * 8);
                     if (!last) {

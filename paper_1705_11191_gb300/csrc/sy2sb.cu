@@ -403,11 +403,27 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         const int r0 = c0 + b;
         const int m = n - r0;
         const int bw = b;
+        T *P = a + r0 + (size_t)c0 * lda;
+        T *V = v1 + r0 + (size_t)c0 * n;
+        T *Tm = t1 + (size_t)c0 * b;
+        int ldt = b;
+        bool panel_done = false;
+        if constexpr (sizeof(T) == 4) {
+            // binary32: TSQR and Householder reconstruction, no grid-wide barrier
+            if (m > 256) {
+                const size_t scr = (size_t)max_g * 64 * 64 * (sizeof(double) / sizeof(T));
+                if ((e = tsqr_panel<T>(st, m, bw, P, lda, V, n, Tm, ldt, reinterpret_cast<T *>(gram),
+                                       scr)) != cudaSuccess)
+                    return e;
+                panel_done = true;
+            }
+        }
         // rows per CTA: 256 (fewer CTAs make the per-column barrier and the reductions of
         // the partials cheaper; the per-column work of a CTA stays small), more if needed
         // for co-residency
         int rows = 256;
         int G = ceil_div(m, rows);
+        if (!panel_done) {
         size_t smem = (size_t)rows * (bw + 1) * sizeof(T);
         size_t smem_t = 2 * (size_t)bw * bw * sizeof(double);
         if (smem < smem_t) smem = smem_t;
@@ -435,14 +451,11 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         pa.part = part; pa.alpha = alpha; pa.wpart = wpart; pa.gram = gram; pa.status = status;
         pa.gstride = max_g;
         pa.spin_limit = spin_limit();
-        T *P = a + r0 + (size_t)c0 * lda;
-        T *V = v1 + r0 + (size_t)c0 * n;
-        T *Tm = t1 + (size_t)c0 * b;
-        int ldt = b;
         void *args[] = {&P, &V, &Tm, &ldt, &pa};
         EGB_COUNT_LAUNCH();
         if ((e = cudaLaunchCooperativeKernel((void *)panel_qr_kernel<T>, dim3(G), dim3(256), args,
                                              smem, st)) != cudaSuccess) return e;
+        }
 
         // ---- two-sided update of A22 = a[r0:, r0:] (full symmetric storage)
         T *A22 = a + r0 + (size_t)r0 * lda;
