@@ -342,7 +342,7 @@ def main():
 def fd_check(egb, torch, n: int, ndirs: int, h: float = 1e-6, kt: float = 0.01) -> dict:
     """Derivatives of the Mermin free energy F = E_band - kT S_ent of the 3D-cluster problem
     of size n (seed 5, N_el = n/4), binary32 + refinement forward, Fermi-Dirac kT = 0.01 Ha,
-    mu bisected to |N(mu) - N_el| <= 1e-12, n_state = N_el/2 + n/10 (enough states that the
+    mu bisected to |N(mu) - N_el| <= 1e-12, n_state = N_el/2 + n/5 (enough states that the
     occupation of the first unused one is below 1e-15). The backward gives dF/dH = P and
     dF/dS = -W (elsi_dm_adjoint_real through KSFreeEnergy). Each of ndirs random symmetric
     directions D (entries N(0,1), seed 6) is checked by central differences:
@@ -352,7 +352,7 @@ def fd_check(egb, torch, n: int, ndirs: int, h: float = 1e-6, kt: float = 0.01) 
     dev = torch.device("cuda")
     t0 = time.perf_counter()
     H, S, nel, _, lam = ksinputs.cluster_problem_torch(n, 5, dev)
-    nstate = min(n, int(nel // 2 + n // 10))
+    nstate = min(n, int(nel // 2 + n // 5))
     gen_s = time.perf_counter() - t0
     hd = egb.Handle(n, nstate, nel)
     hd.use_current_stream()

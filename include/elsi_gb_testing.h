@@ -49,20 +49,6 @@ size_t elsi_gb_q2_work(int n, int b);
 int elsi_gb_q2_apply_f32(int n, int b, const float *v2, const float *tau2, int k, float *z, int ldz,
                          float *work, size_t work_elems, int *status, void *stream);
 
-/*
- * elsi_gb_tsqr_panel_f32: binary32 panel factorisation of the full-to-band reduction
- *   (step (1) of the two-stage method, sec. 3.1, Eq. 11 first line) by tall-skinny QR and
- *   Householder reconstruction. P: device m x bw column-major (ld ldp), m > 256, bw <= 64;
- *   on return its first bw rows hold R (upper triangle, zeros below) and the rows below
- *   are zero. V: device m x bw (ld ldv), the unit lower trapezoidal reflectors; Tm: device
- *   bw x bw (ld ldt), upper triangular, with (I - V T V^T)[:, :bw] R = P (the input) and
- *   I - V T V^T orthogonal. work: device scratch of elsi_gb_tsqr_work(m, bw) floats.
- *   Enqueued on stream (may be NULL). Returns 0, ELSI_ERR_ARG, ELSI_ERR_CUDA.
- */
-size_t elsi_gb_tsqr_work(int m, int bw);
-int elsi_gb_tsqr_panel_f32(int m, int bw, float *P, int ldp, float *V, int ldv, float *Tm, int ldt,
-                           float *work, size_t work_elems, void *stream);
-
 size_t elsi_gb_gemm_f32_work(int m, int n, int k);
 int elsi_gb_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const float *A, int lda,
                      const float *B, int ldb, float beta, float *C, int ldc, int uplo,

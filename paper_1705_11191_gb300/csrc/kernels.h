@@ -126,14 +126,6 @@ cudaError_t apply_q2(cudaStream_t st, int n, int b, const T *v2, const T *tau2, 
 size_t q2_factor_elems(int n, int b);
 cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const float *tau2, int k,
                         float *z, int ldz, float *fac, int *status);
-// Panel QR of the full -> band reduction by TSQR and Householder reconstruction
-// (tsqr.cu): P (m x bw, ld ldp, m > 256) -> R (upper part of P's first bw rows, zeros
-// below), V (m x bw explicit unit lower trapezoidal, ld ldv), T (bw x bw upper, ld ldt)
-// with (I - V T V^T)[:, :bw] R = P. scratch: tsqr_scratch_elems(m, bw) elements.
-size_t tsqr_scratch_elems(int m, int bw);
-template <typename T>
-cudaError_t tsqr_panel(cudaStream_t st, int m, int bw, T *P, int ldp, T *V, int ldv, T *Tm, int ldt,
-                       T *scratch, size_t scratch_elems);
 // Z <- Q1 Z in groups of kQ1Group panels; work: q1_work_elems(b, k) elements.
 constexpr int kQ1Group = 4;
 inline size_t q1_work_elems(int b, int k)

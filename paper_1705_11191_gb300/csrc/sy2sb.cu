@@ -114,17 +114,19 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             colpart[tr][tc] = dv;
             __syncthreads();
             if (tid < bw) wsum[tid] = colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
-            // the reflector's scalars, once (binary64 arithmetic is scarce on this chip)
+            // the reflector's scalars, once, in the panel's precision (one thread's
+            // binary64 square root and two divisions per column cost microseconds on this
+            // chip, whose binary64 units are few)
             if (tid == 0) {
-                const double sigma2 = red[0];
-                const double alpha = __ldcg(prow + j);
-                if (sigma2 == 0.0) { refl[0] = alpha; refl[1] = 0.0; refl[2] = 0.0; }
+                const T sigma2 = (T)red[0];
+                const T alpha = (T)__ldcg(prow + j);
+                if (sigma2 == T(0)) { refl[0] = (double)alpha; refl[1] = 0.0; refl[2] = 0.0; }
                 else {
-                    const double nrm = sqrt(alpha * alpha + sigma2);
-                    const double bt = (alpha >= 0.0) ? -nrm : nrm;
-                    refl[0] = bt;
-                    refl[1] = (bt - alpha) / bt;
-                    refl[2] = 1.0 / (alpha - bt);
+                    const T nrm = dsqrt<T>(fma(alpha, alpha, sigma2));
+                    const T bt = (alpha >= T(0)) ? -nrm : nrm;
+                    refl[0] = (double)bt;
+                    refl[1] = (double)((bt - alpha) / bt);
+                    refl[2] = (double)(T(1) / (alpha - bt));
                 }
             }
             __syncthreads();
@@ -407,23 +409,11 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         T *V = v1 + r0 + (size_t)c0 * n;
         T *Tm = t1 + (size_t)c0 * b;
         int ldt = b;
-        bool panel_done = false;
-        if constexpr (sizeof(T) == 4) {
-            // binary32: TSQR and Householder reconstruction, no grid-wide barrier
-            if (m > 256) {
-                const size_t scr = (size_t)max_g * 64 * 64 * (sizeof(double) / sizeof(T));
-                if ((e = tsqr_panel<T>(st, m, bw, P, lda, V, n, Tm, ldt, reinterpret_cast<T *>(gram),
-                                       scr)) != cudaSuccess)
-                    return e;
-                panel_done = true;
-            }
-        }
         // rows per CTA: 256 (fewer CTAs make the per-column barrier and the reductions of
         // the partials cheaper; the per-column work of a CTA stays small), more if needed
         // for co-residency
         int rows = 256;
         int G = ceil_div(m, rows);
-        if (!panel_done) {
         size_t smem = (size_t)rows * (bw + 1) * sizeof(T);
         size_t smem_t = 2 * (size_t)bw * bw * sizeof(double);
         if (smem < smem_t) smem = smem_t;
@@ -455,7 +445,6 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         EGB_COUNT_LAUNCH();
         if ((e = cudaLaunchCooperativeKernel((void *)panel_qr_kernel<T>, dim3(G), dim3(256), args,
                                              smem, st)) != cudaSuccess) return e;
-        }
 
         // ---- two-sided update of A22 = a[r0:, r0:] (full symmetric storage)
         T *A22 = a + r0 + (size_t)r0 * lda;
