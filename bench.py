@@ -342,70 +342,84 @@ def main():
 def fd_check(egb, torch, n: int, ndirs: int, h: float = 1e-6, kt: float = 0.01) -> dict:
     """Derivatives of the Mermin free energy F = E_band - kT S_ent of the 3D-cluster problem
     of size n (seed 5, N_el = n/4), binary32 + refinement forward, Fermi-Dirac kT = 0.01 Ha,
-    mu bisected to |N(mu) - N_el| <= 1e-12, n_state = N_el/2 + n/5 (enough states that the
-    occupation of the first unused one is below 1e-15). The backward gives dF/dH = P and
-    dF/dS = -W (elsi_dm_adjoint_real through KSFreeEnergy). Each of ndirs random symmetric
-    directions D (entries N(0,1), seed 6) is checked by central differences:
-    (F(H + hD) - F(H - hD)) / 2h against <dF/dH, D>, and likewise for S (S +- hD)."""
+    mu bisected to |N(mu) - N_el| <= 1e-12, n_state = N_el/2 + n/8 (the occupation of the
+    last computed state is reported). The backward gives dF/dH = P and dF/dS = -W
+    (elsi_dm_adjoint_real through KSFreeEnergy). Each of ndirs random symmetric directions
+    D (entries (X + X^T)/2 with X_ij ~ N(0,1), generator seed 6) is checked by central
+    differences, (F(H + hD) - F(H - hD)) / 2h against <dF/dH, D>, and likewise for S.
+    Memory: H, S, the two gradients, D and one density-matrix buffer on the caller's side
+    (6 n^2 binary64 values; H and S are perturbed in place and restored)."""
     import ksinputs
     from paper_1705_11191_gb300 import autograd as ega
     dev = torch.device("cuda")
     t0 = time.perf_counter()
     H, S, nel, _, lam = ksinputs.cluster_problem_torch(n, 5, dev)
-    nstate = min(n, int(nel // 2 + n // 5))
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    nstate = min(n, int(nel // 2 + n // 8))
     gen_s = time.perf_counter() - t0
     hd = egb.Handle(n, nstate, nel)
     hd.use_current_stream()
     hd.set_precision(egb.PREC_FP32_REFINE)
     hd.set_broadening(egb.OCC_FERMI, kt)
     hd.set_occ_accuracy(1e-12)
-    Hr = H.clone().requires_grad_(True)
-    Sr = S.clone().requires_grad_(True)
+    H.requires_grad_(True)
+    S.requires_grad_(True)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    F = ega.free_energy(Hr, Sr, hd)
+    F = ega.free_energy(H, S, hd)
     torch.cuda.synchronize()
     fwd_s = time.perf_counter() - t1
     iters, orth = hd.refine_info()
-    occ = hd.get_occ()
+    occ_last = float(hd.get_occ()[-1])
     t2 = time.perf_counter()
     F.backward()
     torch.cuda.synchronize()
     bwd_s = time.perf_counter() - t2
-    gH, gS = Hr.grad, Sr.grad
-    del Hr, Sr
     F0 = float(F)
+    del F
+    gH, gS = H.grad, S.grad
+    H.requires_grad_(False)
+    S.requires_grad_(False)
+    H.grad = None
+    S.grad = None
+    torch.cuda.empty_cache()
+    Pbuf = torch.empty((n, n), dtype=torch.float64, device=dev)
     gen = torch.Generator(device=dev).manual_seed(6)
     rows = []
 
-    def energy(Hx, Sx):
-        P, e = hd.dm_real(Hx, Sx)
-        del P
+    def energy():
+        _, e = hd.dm_real(H, S, out=Pbuf)
         return e + hd.get_entropy()
 
-    for q in range(ndirs):
-        D = torch.randn((n, n), dtype=torch.float64, device=dev, generator=gen)
-        D = 0.5 * (D + D.T)
-        for which in ("H", "S"):
-            g = gH if which == "H" else gS
-            an = float((g * D).sum())
-            if which == "H":
-                fp, fm = energy(H + h * D, S), energy(H - h * D, S)
-            else:
-                fp, fm = energy(H, S + h * D), energy(H, S - h * D)
-            fd = (fp - fm) / (2.0 * h)
-            rows.append({"dir": q, "wrt": which, "analytic": an, "central_difference": fd,
-                         "rel_err": abs(fd - an) / max(abs(an), 1e-300)})
-        del D
+    with torch.no_grad():
+        for q in range(ndirs):
+            D = torch.randn((n, n), dtype=torch.float64, device=dev, generator=gen)
+            D.add_(D.T.contiguous()).mul_(0.5)
+            torch.cuda.empty_cache()
+            for which, X, g in (("H", H, gH), ("S", S, gS)):
+                an = float((g * D).sum())
+                X.add_(D, alpha=h)
+                fp = energy()
+                X.add_(D, alpha=-2.0 * h)
+                fm = energy()
+                X.add_(D, alpha=h)
+                fd = (fp - fm) / (2.0 * h)
+                rows.append({"dir": q, "wrt": which, "analytic": an, "central_difference": fd,
+                             "abs_err": abs(fd - an), "rel_err": abs(fd - an) / max(abs(an), 1e-300)})
+            del D
     hd.close()
     errs = [r["rel_err"] for r in rows]
+    rms = (sum(r["analytic"] ** 2 for r in rows) / max(1, len(rows))) ** 0.5
     return {"check": "free-energy derivatives by central differences", "n": n,
             "n_electron": nel, "n_state": nstate, "kT": kt, "lambda_min_s": lam,
-            "occ_of_last_state": float(occ[-1]), "F": F0, "refine_iters": iters,
+            "occ_of_last_state": occ_last, "F": F0, "refine_iters": iters,
             "orth_err": orth, "forward_s": fwd_s, "backward_s": bwd_s,
             "input_generation_s": gen_s, "step": h, "directions": ndirs,
             "max_rel_err": max(errs) if errs else None,
-            "median_rel_err": sorted(errs)[len(errs) // 2] if errs else None, "rows": rows}
+            "median_rel_err": sorted(errs)[len(errs) // 2] if errs else None,
+            "max_abs_err": max(r["abs_err"] for r in rows) if rows else None,
+            "rms_analytic": rms, "rows": rows}
 
 
 def _bucket(n: int) -> int:

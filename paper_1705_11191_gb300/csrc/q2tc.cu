@@ -92,18 +92,19 @@ __device__ __forceinline__ int swz(int row, int kk)
 // recurrence on 8 x 8 diagonal blocks merged pairwise (8 -> 16 -> 32 -> 64), and
 // W = -V T^T; writes the hi and lo TF32 planes of V ([a][window row], K = window row) and
 // of W ([window row][a], K = a) in the swizzled operand layout.
-__global__ void __launch_bounds__(256) q2_factor_kernel(int n, int b, int S,
+__global__ void __launch_bounds__(256) q2_factor_kernel(int n, int b, int S, int jb_lo,
                                                         const float *__restrict__ v2,
                                                         const float *__restrict__ tau2,
                                                         float *__restrict__ fac)
 {
-    const int t = blockIdx.x, jb = blockIdx.y;
+    const int t = blockIdx.x, jb = jb_lo + blockIdx.y;
     const int J = jb * kM;
     if (t >= block_steps(n, b, J)) return;
     const int Jend = min(n - 2, J + kM);
     const int w0 = J + t * b;
+    // groups of blocks jb_lo .. are packed from the start of fac
     unsigned char *out = reinterpret_cast<unsigned char *>(
-        fac + (size_t)(group_base(n, b, jb) + t) * kGroupFloats);
+        fac + (size_t)(group_base(n, b, jb) - group_base(n, b, jb_lo) + t) * kGroupFloats);
     extern __shared__ __align__(16) float fsm[];
     float(*Vc)[kM + 1] = reinterpret_cast<float(*)[kM + 1]>(fsm);                 // v_a[i]
     float(*Gm)[kM + 1] = reinterpret_cast<float(*)[kM + 1]>(fsm + kM * (kM + 1));  // v_a . v_c
@@ -270,7 +271,7 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 struct ApplyArgs {
-    int n, b, nblk, k;
+    int n, b, jb_lo, jb_hi, k;  // blocks jb_lo <= jb < jb_hi, their groups packed in fac
     long long ldz;
     const float *fac;
     float *z;
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
     unsigned gidx = 0;  // groups processed by this CTA (parity of every barrier)
 
     // packed index of group (jb, 0), kept up to date as jb decreases
-    long long gbase = a.nblk > 0 ? group_base(n, b, a.nblk - 1) : 0;
+    long long gbase = a.jb_hi > a.jb_lo ? group_base(n, b, a.jb_hi - 1) - group_base(n, b, a.jb_lo) : 0;
     auto fac_of = [&](long long g) -> const unsigned char * {
         return reinterpret_cast<const unsigned char *>(a.fac) + (size_t)g * kGroupBytes;
     };
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
         for (int p = 0; p < 4; ++p)
             bulk_g2s(sW + p * (kWPlane / 2), g + 2 * kVPlane + p * (kWPlane / 2), kWPlane / 2, bar_w);
     };
-    if (tid == 0 && a.nblk > 0) {
+    if (tid == 0 && a.jb_hi > a.jb_lo) {
         const unsigned char *g0 = fac_of(gbase);
         load_v(g0);
         load_w(g0);
@@ -340,11 +341,11 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
     const unsigned idesc2 = idesc_f32acc(2, 128, 128);
     bool ok = true;
 
-    for (int jb = a.nblk - 1; jb >= 0 && ok; --jb) {
+    for (int jb = a.jb_hi - 1; jb >= a.jb_lo && ok; --jb) {
         const int J = jb * kM;
         const int SJ = block_steps(n, b, J);
         // packed index of the group after (jb, t): (jb, t + 1), or (jb - 1, 0) after the last
-        const long long gnext_block = jb > 0 ? gbase - block_steps(n, b, J - kM) : -1;
+        const long long gnext_block = jb > a.jb_lo ? gbase - block_steps(n, b, J - kM) : -1;
         // initial window of the block: rows J .. J+127
 #pragma unroll
         for (int c = 0; c < kChunks; ++c) {
@@ -525,11 +526,33 @@ __global__ void __launch_bounds__(kThreads, 1) q2_apply_tc5_kernel(const ApplyAr
 
 }  // namespace q2tc
 
+// The operand blocks of all groups take about n^2 / (2 * 64 * b) * 128 KB (4.3 GB at
+// n = 16384, b = 64; 26 GB at n = 40000): larger problems are back-transformed a range of
+// blocks at a time (one factor and one apply launch per range), with the blocks of a range
+// holding at most kFacCapBytes.
+constexpr size_t kFacCapBytes = (size_t)6 << 30;
+
+// blocks per range: every range holds at most kFacCapBytes of operand blocks (the largest
+// blocks are the first ones, jb = 0)
+static int q2_blocks_per_range(int n, int b)
+{
+    using namespace q2tc;
+    const int nblk = (n - 2 + kM - 1) / kM;
+    const size_t per_block = (size_t)block_steps(n, b, 0) * kGroupBytes;
+    size_t r = kFacCapBytes / (per_block ? per_block : 1);
+    if (r < 1) r = 1;
+    return (int)(r < (size_t)nblk ? r : (size_t)nblk);
+}
+
 size_t q2_factor_elems(int n, int b)
 {
+    using namespace q2tc;
     if (n < 3) return 1;
-    const int nblk = (n - 2 + q2tc::kM - 1) / q2tc::kM;
-    return (size_t)q2tc::group_base(n, b, nblk) * q2tc::kGroupFloats;
+    const int nblk = (n - 2 + kM - 1) / kM;
+    const int r = q2_blocks_per_range(n, b);
+    // the largest range is the one that starts at block 0
+    const int hi = r < nblk ? r : nblk;
+    return (size_t)group_base(n, b, hi) * kGroupFloats;
 }
 
 cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const float *tau2, int k,
@@ -551,13 +574,21 @@ cudaError_t apply_q2_tc(cudaStream_t st, int n, int b, const float *v2, const fl
                                     kSmemBytes);
     });
     if (e != cudaSuccess) return e;
-    EGB_COUNT_LAUNCH();
-    q2_factor_kernel<<<dim3(S, nblk), 256, fsmem, st>>>(n, b, S, v2, tau2, fac);
-    ApplyArgs a;
-    a.n = n; a.b = b; a.nblk = nblk; a.k = k; a.ldz = ldz; a.fac = fac; a.z = z; a.status = status;
-    EGB_COUNT_LAUNCH();
-    q2_apply_tc5_kernel<<<ceil_div(k, kCols), kThreads, kSmemBytes, st>>>(a);
-    return cudaGetLastError();
+    // ranges of blocks from the last (applied first) to the first
+    const int per = q2_blocks_per_range(n, b);
+    for (int hi = nblk; hi > 0; hi -= per) {
+        const int lo = hi - per > 0 ? hi - per : 0;
+        EGB_COUNT_LAUNCH();
+        q2_factor_kernel<<<dim3(S, hi - lo), 256, fsmem, st>>>(n, b, S, lo, v2, tau2, fac);
+        ApplyArgs a;
+        a.n = n; a.b = b; a.jb_lo = lo; a.jb_hi = hi; a.k = k; a.ldz = ldz; a.fac = fac; a.z = z;
+        a.status = status;
+        EGB_COUNT_LAUNCH();
+        q2_apply_tc5_kernel<<<ceil_div(k, kCols), kThreads, kSmemBytes, st>>>(a);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) return le;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace egb
