@@ -185,8 +185,12 @@ cudaError_t ozaki_split(cudaStream_t st, int V, int K, const double *src, long l
                         __nv_bfloat16 *planes, int *exps);
 // C (m x n, ldc) = alpha * A B + beta * C with A given by the split of its m rows and B
 // by the split of its n columns (both of length k). uplo = 1: lower triangle only.
+// digits (1..7, default 7): leading digit planes used, i.e. D(D+1)/2 digit products and a
+// truncation error of about 2^(-7(D+1)) relative to max|A_i.| max|B_.j| per product term.
+constexpr int kOzDigits = 7;
 cudaError_t ozaki_gemm(cudaStream_t st, int m, int n, int k, double alpha,
                        const __nv_bfloat16 *Ad, const int *ea, const __nv_bfloat16 *Bd,
-                       const int *eb, double beta, double *C, int ldc, int uplo);
+                       const int *eb, double beta, double *C, int ldc, int uplo,
+                       int digits = kOzDigits);
 
 }  // namespace egb

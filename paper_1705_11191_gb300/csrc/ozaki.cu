@@ -149,6 +149,7 @@ struct Maps {
 
 struct Args {
     int m_real, n_real, kpad, mpad, npad, uplo, ldc;
+    int digits;  // D <= kOzD: digit planes used per operand (levels 2 .. D + 1)
     const int *ea, *eb;
     double alpha, beta;
     double *C;
@@ -195,8 +196,8 @@ ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a
         if (lane == 0) {
             int it = 0;
             bool stop = false;
-            for (int L = kOzD + 1; L >= 2 && !stop; --L) {
-                const int s_lo = max(1, L - kOzD), s_hi = min(kOzD, L - 1);
+            for (int L = a.digits + 1; L >= 2 && !stop; --L) {
+                const int s_lo = max(1, L - a.digits), s_hi = min(a.digits, L - 1);
                 for (int c = 0; c < nch && !stop; ++c) {
                     const int kt1 = min(nkt, (c + 1) * CHUNK_TILES);
                     for (int sa = s_lo; sa <= s_hi && !stop; ++sa)
@@ -225,8 +226,8 @@ ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a
             const unsigned idesc = idesc_f32acc(1, BM, BN);
             int it = 0, g = 0;
             bool stop = false;
-            for (int L = kOzD + 1; L >= 2 && !stop; --L) {
-                const int s_lo = max(1, L - kOzD), s_hi = min(kOzD, L - 1);
+            for (int L = a.digits + 1; L >= 2 && !stop; --L) {
+                const int s_lo = max(1, L - a.digits), s_hi = min(a.digits, L - 1);
                 for (int c = 0; c < nch && !stop; ++c, ++g) {
                     const int bsel = g & 1;
                     if (g >= 2 && !mbar_wait(acce0 + 8 * bsel, ((g >> 1) - 1) & 1)) {
@@ -269,7 +270,7 @@ ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a
         int iacc[BN];
         bool ok = true;
         int g = 0;
-        for (int L = kOzD + 1; L >= 2 && ok; --L) {
+        for (int L = a.digits + 1; L >= 2 && ok; --L) {
 #pragma unroll
             for (int j = 0; j < BN; ++j) iacc[j] = 0;
             for (int c = 0; c < nch; ++c, ++g) {
@@ -296,7 +297,7 @@ ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a
             }
             if (!ok || row >= a.m_real) continue;
             // C (+)= alpha 2^(e_i + f_j - 7L) level sum, 16 columns at a time
-            const bool firstL = (L == kOzD + 1);
+            const bool firstL = (L == a.digits + 1);
             double *crow = a.C + (size_t)row;
 #pragma unroll
             for (int q = 0; q < BN / 16; ++q) {
@@ -350,8 +351,9 @@ cudaError_t ozaki_split(cudaStream_t st, int V, int K, const double *src, long l
 
 cudaError_t ozaki_gemm(cudaStream_t st, int m, int n, int k, double alpha,
                        const __nv_bfloat16 *Ad, const int *ea, const __nv_bfloat16 *Bd,
-                       const int *eb, double beta, double *C, int ldc, int uplo)
+                       const int *eb, double beta, double *C, int ldc, int uplo, int digits)
 {
+    if (digits < 1 || digits > kOzD) return cudaErrorInvalidValue;
     using namespace oztc;
     if (m <= 0 || n <= 0) return cudaSuccess;
     const int mpad = ceil_div(m, kOzBM) * kOzBM, npad = ceil_div(n, kOzBN) * kOzBN;
@@ -365,6 +367,7 @@ cudaError_t ozaki_gemm(cudaStream_t st, int m, int n, int k, double alpha,
     Args a;
     a.m_real = m; a.n_real = n; a.kpad = kpad; a.mpad = mpad; a.npad = npad; a.uplo = uplo;
     a.ldc = ldc; a.ea = ea; a.eb = eb; a.alpha = alpha; a.beta = beta; a.C = C;
+    a.digits = digits;
     float *tw;
     size_t te;
     int *ts = nullptr;

@@ -469,16 +469,20 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     if (S64) CKR(ozaki_split(st, n, n, S64, n, 1, nullptr, nullptr, SDG, eS));
 
     // products, cluster Rayleigh-Ritz rotation and the Rayleigh quotients of the
-    // current X_o (steps shared by every iteration and the final polish)
-    auto products_and_rr = [&]() -> int {
+    // current X_o (steps shared by every iteration and the final polish). digits: digit
+    // planes of the binary64-accurate products; an iteration only needs its products
+    // accurate to well below the error it corrects, so the first iterations (errors of
+    // about 1e-3 and 1e-5 in X) use 4 and 5 of the 7 digits (10 and 15 digit products
+    // instead of 28; truncation about 2^-35 and 2^-42 relative), the later ones all 7.
+    auto products_and_rr = [&](int digits) -> int {
         CKR(ozaki_split(st, k, n, XO, n, 1, nullptr, nullptr, XDG, eX));
-        CKR(ozaki_gemm(st, n, k, n, 1.0, HDG, eH, XDG, eX, 0.0, YH, n, 0));
-        if (S64) CKR(ozaki_gemm(st, n, k, n, 1.0, SDG, eS, XDG, eX, 0.0, YS, n, 0));
+        CKR(ozaki_gemm(st, n, k, n, 1.0, HDG, eH, XDG, eX, 0.0, YH, n, 0, digits));
+        if (S64) CKR(ozaki_gemm(st, n, k, n, 1.0, SDG, eS, XDG, eX, 0.0, YS, n, 0, digits));
         else CKR(cudaMemcpyAsync(YS, XO, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
         CKR(ozaki_split(st, k, n, YH, n, 1, nullptr, nullptr, YHDG, eYH));
         CKR(ozaki_split(st, k, n, YS, n, 1, nullptr, nullptr, YSDG, eYS));
-        CKR(ozaki_gemm(st, k, k, n, 1.0, XDG, eX, YHDG, eYH, 0.0, GOO, k, 0));
-        CKR(ozaki_gemm(st, k, k, n, 1.0, XDG, eX, YSDG, eYS, 0.0, SOO, k, 0));
+        CKR(ozaki_gemm(st, k, k, n, 1.0, XDG, eX, YHDG, eYH, 0.0, GOO, k, 0, digits));
+        CKR(ozaki_gemm(st, k, k, n, 1.0, XDG, eX, YSDG, eYS, 0.0, SOO, k, 0, digits));
         // X^T H X and X^T S X are symmetric; rounding of the two products is not, and an
         // antisymmetric error would enter E_ij + E_ji (the re-orthonormalisation) divided
         // by lambda_j - lambda_i. Use the symmetric parts.
@@ -501,7 +505,7 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     int iters = 0;
     double emax = 1.0;
     for (int it = 0; it < h->refine_max_iter; ++it) {
-        int rc = products_and_rr();
+        int rc = products_and_rr(it == 0 ? 4 : (it == 1 ? 5 : kOzDigits));
         if (rc) return rc;
         // M = Xu^T R_o in binary32
         if (n > k)
@@ -526,7 +530,7 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     }
     // final polish: Rayleigh-Ritz inside clusters, Rayleigh quotients, orthonormality
     {
-        int rc = products_and_rr();
+        int rc = products_and_rr(kOzDigits);
         if (rc) return rc;
         CKR(cudaMemsetAsync(STATS, 0, 4 * sizeof(unsigned long long), st));
         EGB_COUNT_LAUNCH();
