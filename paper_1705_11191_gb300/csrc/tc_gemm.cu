@@ -61,6 +61,20 @@ struct Maps {
 // buffer. The tensor-memory accumulation is not rounded to nearest, so its error grows with
 // the number of MMAs summed into one accumulator and with that accumulator's magnitude;
 // short chunks and the separate small sum keep it at the binary32 level.
+//
+// Persistent: one CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (row tile fastest; with uplo the tiles strictly above the diagonal are skipped), all three
+// roles in the same order, so that the k-tile ring and the two accumulator buffers keep
+// their phases across tiles: while the epilogue warps read-modify-write C for one tile the
+// MMA issuer already fills the accumulator buffers with the next tile's first chunks and the
+// producer keeps the ring full.
+__device__ __forceinline__ bool tile_of(int t, int tiles_m, int uplo, int *m0, int *n0)
+{
+    *m0 = (t % tiles_m) * BM;
+    *n0 = (t / tiles_m) * BN;
+    return !(uplo && *m0 + BM - 1 < *n0);  // false: strictly above the diagonal
+}
+
 __global__ void __launch_bounds__(192, 1)
 gemm_tf32x3_kernel(const __grid_constant__ Maps maps, int m, int n, int kp, float alpha,
                    float beta, float *__restrict__ C, int ldc, int uplo, int *status)
@@ -73,8 +87,8 @@ gemm_tf32x3_kernel(const __grid_constant__ Maps maps, int m, int n, int kp, floa
     __shared__ int aborted;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    if (uplo && m0 + BM - 1 < n0) return;  // tile strictly above the diagonal
+    const int tiles_m = (m + BM - 1) / BM, tiles_n = (n + BN - 1) / BN;
+    const int ntiles = tiles_m * tiles_n;
     const int nk = kp / BK;
     const int nchunk = (nk + CH - 1) / CH;
     const unsigned full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
@@ -98,114 +112,136 @@ gemm_tf32x3_kernel(const __grid_constant__ Maps maps, int m, int n, int kp, floa
     tc_fence_after();
     const unsigned tmem = *tmem_slot;
 
-    int armed = 0;  // producer: stages loaded
+    int armed = 0;  // producer: k-tiles loaded (over all tiles of this CTA)
     if (warp == 0) {
         if (lane == 0) {
-            for (int kt = 0; kt < nk; ++kt) {
-                const int s = kt % STAGES;
-                const unsigned ph = (kt / STAGES) & 1;
-                if (kt >= STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1)) {
-                    report_error(status, ELSI_ERR_TIMEOUT, 1);
-                    atomicExch(&aborted, 1);
-                    break;
+            int ktg = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+                int m0, n0;
+                if (!tile_of(t, tiles_m, uplo, &m0, &n0)) continue;
+                for (int kt = 0; kt < nk; ++kt, ++ktg) {
+                    const int s = ktg % STAGES;
+                    const unsigned ph = (ktg / STAGES) & 1;
+                    if (ktg >= STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1)) {
+                        report_error(status, ELSI_ERR_TIMEOUT, 1);
+                        atomicExch(&aborted, 1);
+                        stop = true;
+                        break;
+                    }
+                    if (*(volatile int *)&aborted) { stop = true; break; }
+                    unsigned char *st = smem + s * STAGE_BYTES;
+                    const unsigned full = full0 + 8 * s;
+                    mbar_expect_tx(full, STAGE_BYTES);
+                    tma_load_2d(smem_u32(st), &maps.a_hi, full, kt * BK, m0);
+                    tma_load_2d(smem_u32(st + TILE_BYTES), &maps.a_lo, full, kt * BK, m0);
+                    tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &maps.b_hi, full, kt * BK, n0);
+                    tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &maps.b_lo, full, kt * BK, n0);
+                    armed = ktg + 1;
                 }
-                if (*(volatile int *)&aborted) break;
-                unsigned char *st = smem + s * STAGE_BYTES;
-                const unsigned full = full0 + 8 * s;
-                mbar_expect_tx(full, STAGE_BYTES);
-                tma_load_2d(smem_u32(st), &maps.a_hi, full, kt * BK, m0);
-                tma_load_2d(smem_u32(st + TILE_BYTES), &maps.a_lo, full, kt * BK, m0);
-                tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &maps.b_hi, full, kt * BK, n0);
-                tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &maps.b_lo, full, kt * BK, n0);
-                armed = kt + 1;
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const unsigned idesc = idesc_f32acc(2, BM, BN);
-            for (int kt = 0; kt < nk; ++kt) {
-                const int s = kt % STAGES, g = kt / CH, bsel = g & 1;
-                const unsigned ph = (kt / STAGES) & 1;
-                const bool first = (kt % CH) == 0;
-                if (first && g >= 2 && !mbar_wait(acce0 + 8 * bsel, ((g >> 1) - 1) & 1)) {
-                    report_error(status, ELSI_ERR_TIMEOUT, 4);
-                    atomicExch(&aborted, 1);
-                    break;
-                }
-                if (!mbar_wait(full0 + 8 * s, ph)) {
-                    report_error(status, ELSI_ERR_TIMEOUT, 2);
-                    atomicExch(&aborted, 1);
-                    break;
-                }
-                tc_fence_after();
-                const unsigned base = smem_u32(smem + s * STAGE_BYTES);
-                const unsigned d = tmem + bsel * 2 * BN;  // hi*hi sum; cross terms at + BN
+            int ktg = 0, gbase = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+                int m0, n0;
+                if (!tile_of(t, tiles_m, uplo, &m0, &n0)) continue;
+                for (int kt = 0; kt < nk; ++kt, ++ktg) {
+                    const int s = ktg % STAGES, g = gbase + kt / CH, bsel = g & 1;
+                    const unsigned ph = (ktg / STAGES) & 1;
+                    const bool first = (kt % CH) == 0;
+                    if (first && g >= 2 && !mbar_wait(acce0 + 8 * bsel, ((g >> 1) - 1) & 1)) {
+                        report_error(status, ELSI_ERR_TIMEOUT, 4);
+                        atomicExch(&aborted, 1);
+                        stop = true;
+                        break;
+                    }
+                    if (!mbar_wait(full0 + 8 * s, ph)) {
+                        report_error(status, ELSI_ERR_TIMEOUT, 2);
+                        atomicExch(&aborted, 1);
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned base = smem_u32(smem + s * STAGE_BYTES);
+                    const unsigned d = tmem + bsel * 2 * BN;  // hi*hi sum; cross terms at + BN
 #pragma unroll
-                for (int kk = 0; kk < BK / 8; ++kk) {
-                    const unsigned off = kk * 32;  // 8 tf32 = 32 bytes along K
-                    const unsigned long long ah = sdesc(base + off), al = sdesc(base + TILE_BYTES + off);
-                    const unsigned long long bh = sdesc(base + 2 * TILE_BYTES + off);
-                    const unsigned long long bl = sdesc(base + 3 * TILE_BYTES + off);
-                    const unsigned acc = (first && kk == 0) ? 0u : 1u;
-                    mma_tf32(d + BN, al, bh, idesc, acc);
-                    mma_tf32(d + BN, ah, bl, idesc, 1u);
-                    mma_tf32(d, ah, bh, idesc, acc);
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        const unsigned off = kk * 32;  // 8 tf32 = 32 bytes along K
+                        const unsigned long long ah = sdesc(base + off), al = sdesc(base + TILE_BYTES + off);
+                        const unsigned long long bh = sdesc(base + 2 * TILE_BYTES + off);
+                        const unsigned long long bl = sdesc(base + 3 * TILE_BYTES + off);
+                        const unsigned acc = (first && kk == 0) ? 0u : 1u;
+                        mma_tf32(d + BN, al, bh, idesc, acc);
+                        mma_tf32(d + BN, ah, bl, idesc, 1u);
+                        mma_tf32(d, ah, bh, idesc, acc);
+                    }
+                    mma_commit(empty0 + 8 * s);
+                    if ((kt % CH) == CH - 1 || kt == nk - 1) mma_commit(accf0 + 8 * bsel);
                 }
-                mma_commit(empty0 + 8 * s);
-                if ((kt % CH) == CH - 1 || kt == nk - 1) mma_commit(accf0 + 8 * bsel);
+                gbase += nchunk;
             }
         }
     } else {
         const int quarter = warp & 3;
-        float acc[BN];
-#pragma unroll
-        for (int j = 0; j < BN; ++j) acc[j] = 0.0f;
         bool ok = true;
-        for (int g = 0; g < nchunk && ok; ++g) {
-            const int bsel = g & 1;
-            ok = mbar_wait(accf0 + 8 * bsel, (g >> 1) & 1);
-            if (!ok) {
-                if (lane == 0) {
-                    report_error(status, ELSI_ERR_TIMEOUT, 3);
-                    atomicExch(&aborted, 1);
+        int gbase = 0;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            int m0, n0;
+            if (!tile_of(t, tiles_m, uplo, &m0, &n0)) continue;
+            float acc[BN];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) acc[j] = 0.0f;
+            for (int c = 0; c < nchunk && ok; ++c) {
+                const int g = gbase + c, bsel = g & 1;
+                ok = mbar_wait(accf0 + 8 * bsel, (g >> 1) & 1);
+                if (!ok) {
+                    if (lane == 0) {
+                        report_error(status, ELSI_ERR_TIMEOUT, 3);
+                        atomicExch(&aborted, 1);
+                    }
+                    break;
                 }
-                break;
-            }
-            tc_fence_after();
+                tc_fence_after();
 #pragma unroll
-            for (int q = 0; q < BN / 32; ++q) {
-                float v[32];
-                const unsigned ta = tmem + ((unsigned)(quarter * 32) << 16) + bsel * 2 * BN + q * 32;
-                tmem_ld32(ta + BN, v);  // cross terms
+                for (int q = 0; q < BN / 32; ++q) {
+                    float v[32];
+                    const unsigned ta = tmem + ((unsigned)(quarter * 32) << 16) + bsel * 2 * BN + q * 32;
+                    tmem_ld32(ta + BN, v);  // cross terms
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc[q * 32 + j] += v[j];
-                tmem_ld32(ta, v);  // hi * hi
+                    for (int j = 0; j < 32; ++j) acc[q * 32 + j] += v[j];
+                    tmem_ld32(ta, v);  // hi * hi
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc[q * 32 + j] += v[j];
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acce0 + 8 * bsel);
-        }
-        const int row = m0 + quarter * 32 + lane;
-        if (ok && row < m) {
-            // 16 columns at a time: all loads of C first (independent, in flight together),
-            // then the stores; each column is one 128-byte line per warp.
-            float *crow = C + (size_t)row;
-#pragma unroll
-            for (int q = 0; q < BN / 16; ++q) {
-                float cv[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + q * 16 + j;
-                    const bool in = col < n && (!uplo || row >= col);
-                    cv[j] = (beta != 0.0f && in) ? crow[(size_t)col * ldc] : 0.0f;
+                    for (int j = 0; j < 32; ++j) acc[q * 32 + j] += v[j];
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce0 + 8 * bsel);
+            }
+            gbase += nchunk;
+            const int row = m0 + quarter * 32 + lane;
+            if (ok && row < m) {
+                // 16 columns at a time: all loads of C first (independent, in flight
+                // together), then the stores; each column is one 128-byte line per warp.
+                float *crow = C + (size_t)row;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + q * 16 + j;
-                    if (col < n && (!uplo || row >= col))
-                        crow[(size_t)col * ldc] = alpha * acc[q * 16 + j] + beta * cv[j];
+                for (int q = 0; q < BN / 16; ++q) {
+                    float cv[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + q * 16 + j;
+                        const bool in = col < n && (!uplo || row >= col);
+                        cv[j] = (beta != 0.0f && in) ? crow[(size_t)col * ldc] : 0.0f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + q * 16 + j;
+                        if (col < n && (!uplo || row >= col))
+                            crow[(size_t)col * ldc] = alpha * acc[q * 16 + j] + beta * cv[j];
+                    }
                 }
             }
         }
@@ -316,7 +352,18 @@ cudaError_t tc_gemm_f32_parts(cudaStream_t st, int m, int n, int nparts, const T
         return cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     });
     if (attr_err != cudaSuccess) return attr_err;
-    dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN);
+    // persistent: one CTA per SM (the ring takes 192 KB of shared memory), at most one per tile
+    static int sms[kMaxDevices] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int nsm = (dev >= 0 && dev < kMaxDevices) ? sms[dev] : 0;
+    if (nsm <= 0) {
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 1;
+        if (dev >= 0 && dev < kMaxDevices) sms[dev] = nsm;
+    }
+    const long long ntiles = (long long)((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+    const int grid = (int)(ntiles < nsm ? ntiles : nsm);
     EGB_COUNT_LAUNCH();
     gemm_tf32x3_kernel<<<grid, 192, SMEM_BYTES, st>>>(maps, m, n, kp, alpha, beta, C, ldc, uplo, status);
     return cudaGetLastError();
