@@ -568,7 +568,7 @@ _STAGE_KERNEL = {
     "full_to_band": ("panel_qr_kernel + w_stage kernels + gemm_tf32x3_kernel", "tf32"),
     "band_to_tri": ("chase_kernel", None),
     "tridiag_solve": ("bisect_kernel + twisted_kernel", None),
-    "back_q2": ("q2_apply_tc_kernel", "tf32"),
+    "back_q2": ("q2_apply_tc5_kernel (two launches: block ranges) + q2_factor_kernel", "tf32"),
     "back_q1": ("gemm_tf32x3_kernel", "tf32"),
     "back_subst": ("gemm_tf32x3_kernel (blocked triangular solve)", "tf32"),
     "refine": ("ozaki_gemm_tc_kernel (all launches of the stage)", "bf16"),
@@ -576,6 +576,33 @@ _STAGE_KERNEL = {
     "density": ("ozaki_gemm_tc_kernel (P and W)", "bf16"),
 }
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tf32 / bf16 tensor rates
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a stage's kernels from one
+# ncu capture, valid while the kernel's source file is unchanged (sha256 prefix). The Q2
+# capture is at n = 8192 (the n = 16384 workspace is too large for a multi-pass capture);
+# its traffic is one read and one write of the remaining rows of Z per block of 64 sweeps,
+# which grows as n^3 once Z exceeds L2 (as it does at 8192 and 16384), so it is scaled by
+# (n / 8192)^3.
+MEASURED_TRAFFIC = {
+    "back_q2": {"kernel": "q2_apply_tc5_kernel", "source": "paper_1705_11191_gb300/csrc/q2tc.cu",
+                "sha256_16": "a7bd6373b70be307", "n": 8192, "bytes": 15318903552 + 16249897472},
+}
+
+
+def stage_traffic(stage: str, n: int):
+    """Traffic per solve of the stage's kernels at size n, or None when no capture matches."""
+    import hashlib
+    m = MEASURED_TRAFFIC.get(stage)
+    if not m or n < m["n"]:
+        return None
+    try:
+        with open(os.path.join(ROOT, m["source"]), "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if sha != m["sha256_16"]:
+        return None  # the kernel changed since the counters were taken
+    return m["bytes"] * (n / m["n"]) ** 3
 OZAKI_PRODUCTS = 28  # bf16 digit products per binary64-accurate product (7 digits, 8 levels)
 
 
@@ -629,7 +656,8 @@ def roofline_for(stage: str, stage_ms: float, n: int, k: int, prec: int, clocks:
     kern, dt = _STAGE_KERNEL.get(stage, (stage, None))
     if prec == 0:
         dt = None
-    out = {"stage": stage, "kernel": kern, "ms": round(stage_ms, 3), "traffic": None}
+    out = {"stage": stage, "kernel": kern, "ms": round(stage_ms, 3),
+           "traffic": stage_traffic(stage, n) if prec == 1 else None}
     sec = stage_ms * 1e-3
     work, unit = stage_work(stage, n, k, prec, refine_iters, band)
     if unit == "bytes":
