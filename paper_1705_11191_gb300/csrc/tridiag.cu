@@ -28,16 +28,35 @@ __device__ __forceinline__ double guard_pivot(double q, double pivmin)
     return (fabs(q) < pivmin) ? -pivmin : q;
 }
 
-// number of eigenvalues < sigma
+// number of eigenvalues < sigma: the sign changes of the leading principal minors
+// p_i = det(T[0:i, 0:i] - sigma I), p_0 = 1, p_{i+1} = (d_i - sigma) p_i - e_{i-1}^2 p_{i-1}
+// (Sturm; Givens 1954). The ratio q_i = p_{i+1} / p_i is the pivot of the LDL^T
+// factorisation of T - sigma I, and a pivot smaller than pivmin in magnitude is replaced
+// by -pivmin as in the pivot form. This form needs no division (binary64 division is a long
+// sequence of the few binary64 FMA units of this chip); the pair (p_i, p_{i-1}) is rescaled
+// by an exact power of two whenever |p_i| leaves [2^-600, 2^600] (checked every 8 steps;
+// one step changes |p| by at most a factor of about 2 ||T|| / pivmin, far below 2^50).
 __device__ int sturm_count(int n, const double *__restrict__ d, const double *__restrict__ e,
                            double sigma, double pivmin)
 {
-    double q = guard_pivot(d[0] - sigma, pivmin);
-    int cnt = q < 0.0;
-    for (int i = 1; i < n; ++i) {
-        double ei = e[i - 1];
-        q = guard_pivot(d[i] - sigma - ei * ei / q, pivmin);
-        cnt += q < 0.0;
+    double pm = 1.0;                                // p_{i-1}
+    double p = guard_pivot(d[0] - sigma, pivmin);   // p_1 = q_0
+    int cnt = p < 0.0;
+    int i = 1;
+    while (i < n) {
+        const int iend = min(n, i + 8);
+        for (; i < iend; ++i) {
+            const double ei = e[i - 1];
+            double pn = fma(d[i] - sigma, p, -(ei * ei) * pm);
+            // pivot q = pn / p below pivmin in magnitude: q = -pivmin
+            if (fabs(pn) < pivmin * fabs(p)) pn = -pivmin * p;
+            cnt += (pn < 0.0) != (p < 0.0);
+            pm = p;
+            p = pn;
+        }
+        const double ap = fabs(p);
+        if (ap > 0x1p600) { p *= 0x1p-600; pm *= 0x1p-600; }
+        else if (ap < 0x1p-600) { p *= 0x1p600; pm *= 0x1p600; }
     }
     return cnt;
 }
