@@ -54,6 +54,29 @@ int elsi_gb_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const flo
                      const float *B, int ldb, float beta, float *C, int ldc, int uplo,
                      float *work, size_t work_elems, int *status, void *stream);
 
+/*
+ * elsi_gb_gemm_f64_digits: the binary64-accurate product of the refinement and of P, W
+ *   (Ozaki et al., Numer. Algorithms 59 (2012), integer-digit form):
+ *   C (m x n, column-major, ldc) = alpha * op(A) op(B) + beta * C, op() as for
+ *   elsi_gb_gemm_f32, every row of op(A) and column of op(B) cut into `digits` (1..7)
+ *   signed 7-bit digits after scaling by a power of two, the digit products summed
+ *   exactly on the bf16 tensor cores, levels 2..digits+1 kept (truncation about
+ *   2^(-7 digits) relative to max|op(A)_i.| max|op(B)_.j| per term). uplo = 1 writes
+ *   only the lower triangle of C. planes: device scratch of
+ *   elsi_gb_gemm_f64_digits_planes(m, n, k) bf16 values (2 bytes each; 16-byte aligned);
+ *   exps: device int[elsi_gb_gemm_f64_digits_exps(m, n)]; status: device int[8], zeroed
+ *   by the caller (ELSI_ERR_TIMEOUT if a pipeline wait expired). Any k >= 1 (products
+ *   longer than 32768 run as several K segments added in binary64). Enqueued on stream
+ *   (may be NULL). Returns 0, ELSI_ERR_ARG for bad sizes, digits or scratch,
+ *   ELSI_ERR_CUDA.
+ */
+size_t elsi_gb_gemm_f64_digits_planes(int m, int n, int k);
+size_t elsi_gb_gemm_f64_digits_exps(int m, int n);
+int elsi_gb_gemm_f64_digits(int ta, int tb, int m, int n, int k, double alpha, const double *A,
+                            int lda, const double *B, int ldb, double beta, double *C, int ldc,
+                            int uplo, int digits, void *planes, size_t plane_elems, int *exps,
+                            size_t exp_elems, int *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -143,7 +143,7 @@ void set_f64_tc_scratch(__nv_bfloat16 *planes, size_t elems, int *exps, size_t e
 // rows, op(B) by columns (once for A A^T). cudaErrorNotSupported if the scratch is short.
 static cudaError_t gemm_f64_digits(cudaStream_t st, int ta, int tb, int m, int n, int k, double alpha,
                                    const double *A, int lda, const double *B, int ldb, double beta,
-                                   double *C, int ldc, int uplo)
+                                   double *C, int ldc, int uplo, int digits = kOzDigits)
 {
     const bool same = A == B && lda == ldb && ta != tb && m == n;
     const size_t ea = ozaki_split_elems(m, k), eb = same ? 0 : ozaki_split_elems(n, k);
@@ -159,7 +159,7 @@ static cudaError_t gemm_f64_digits(cudaStream_t st, int ta, int tb, int m, int n
     if (!same &&
         (e = ozaki_split(st, n, k, B, tb ? 1 : ldb, tb ? ldb : 1, nullptr, nullptr, bd, ye)) != cudaSuccess)
         return e;
-    return ozaki_gemm(st, m, n, k, alpha, ad, xe, bd, ye, beta, C, ldc, uplo);
+    return ozaki_gemm(st, m, n, k, alpha, ad, xe, bd, ye, beta, C, ldc, uplo, digits);
 }
 
 template <typename T>
@@ -393,3 +393,43 @@ template cudaError_t check_finite<double>(cudaStream_t, int, int, const double *
 template cudaError_t check_finite<float>(cudaStream_t, int, int, const float *, int, int *);
 
 }  // namespace egb
+
+extern "C" size_t elsi_gb_gemm_f64_digits_planes(int m, int n, int k)
+{
+    if (m < 1 || n < 1 || k < 1) return 0;
+    return egb::ozaki_split_elems(m, k) + egb::ozaki_split_elems(n, k);
+}
+
+extern "C" size_t elsi_gb_gemm_f64_digits_exps(int m, int n)
+{
+    if (m < 1 || n < 1) return 0;
+    return (size_t)egb::ceil_div(m, 128) * 128 + (size_t)egb::ceil_div(n, 128) * 128;
+}
+
+extern "C" int elsi_gb_gemm_f64_digits(int ta, int tb, int m, int n, int k, double alpha,
+                                       const double *A, int lda, const double *B, int ldb,
+                                       double beta, double *C, int ldc, int uplo, int digits,
+                                       void *planes, size_t plane_elems, int *exps, size_t exp_elems,
+                                       int *status, void *stream)
+{
+    if (m < 1 || n < 1 || k < 1 || digits < 1 || digits > egb::kOzDigits || !A || !B || !C || !planes ||
+        !exps || !status)
+        return ELSI_ERR_ARG;
+    if (ldc < m || lda < (ta ? k : m) || ldb < (tb ? n : k)) return ELSI_ERR_ARG;
+    if ((size_t)planes % 16 != 0 || plane_elems < elsi_gb_gemm_f64_digits_planes(m, n, k) ||
+        exp_elems < elsi_gb_gemm_f64_digits_exps(m, n))
+        return ELSI_ERR_ARG;
+    // the pipeline's status word comes from the binary32 scratch slot of this thread
+    float *tw;
+    size_t te;
+    int *ts;
+    egb::tc_scratch(&tw, &te, &ts);
+    egb::set_tc_scratch(tw, te, status);
+    egb::set_f64_tc_scratch(reinterpret_cast<__nv_bfloat16 *>(planes), plane_elems, exps, exp_elems);
+    cudaError_t e = egb::gemm_f64_digits((cudaStream_t)stream, ta, tb, m, n, k, alpha, A, lda, B, ldb,
+                                         beta, C, ldc, uplo, digits);
+    egb::set_f64_tc_scratch(nullptr, 0, nullptr, 0);
+    egb::set_tc_scratch(tw, te, ts);
+    if (e == cudaErrorNotSupported) return ELSI_ERR_ARG;
+    return e == cudaSuccess ? ELSI_OK : ELSI_ERR_CUDA;
+}

@@ -15,6 +15,10 @@
 // (exact), and each level is finally scaled and added in binary64. Levels L = 2..D+1 are
 // kept, which leaves a truncation error of about 2^{-7(D+1)} relative to
 // max|A_i.| max|B_.j| per product term.
+//
+// One chunk of level L sums at most 256 (2 * 128 * 64 + (D - 2) * 64 * 64) < 9.5e6 in
+// magnitude, so the int32 level sum is exact for up to 227 chunks (K = 58 112); longer
+// products are cut along K into segments of kOzSegK and the segments added in binary64.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -26,6 +30,7 @@ namespace egb {
 constexpr int kOzD = 7;         // digits per operand
 constexpr int kOzBits = 7;      // bits per digit
 constexpr int kOzBM = 128, kOzBN = 128, kOzBK = 16;  // plane padding: rows, K
+constexpr int kOzSegK = 32768;  // K per kernel launch (128 chunks of 256: int32-exact sums)
 
 // ------------------------------------------------------------------ splitting
 // The digits are those of the binary64 steps r = x 2^-e, then for s = 1..D: t = 128 r,
@@ -149,6 +154,7 @@ struct Maps {
 
 struct Args {
     int m_real, n_real, kpad, mpad, npad, uplo, ldc;
+    int kt0;     // first k-tile of this launch's K segment; kpad is the segment's end
     int digits;  // D <= kOzD: digit planes used per operand (levels 2 .. D + 1)
     const int *ea, *eb;
     double alpha, beta;
@@ -173,7 +179,7 @@ ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     if (m0 >= a.m_real || n0 >= a.n_real) return;
     if (a.uplo && m0 + BM - 1 < n0) return;  // tile strictly above the diagonal
-    const int nkt = (a.kpad + BK - 1) / BK;
+    const int nkt = (a.kpad + BK - 1) / BK - a.kt0;  // k-tiles of this segment
     const int nch = (nkt + CHUNK_TILES - 1) / CHUNK_TILES;
     const unsigned full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
     const unsigned accf0 = smem_u32(&bars[2 * STAGES]), acce0 = smem_u32(&bars[2 * STAGES + 2]);
@@ -213,8 +219,9 @@ ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a
                             unsigned char *dst = smem + st * STAGE_BYTES;
                             const unsigned full = full0 + 8 * st;
                             mbar_expect_tx(full, STAGE_BYTES);
-                            tma_load_2d(smem_u32(dst), &maps.a, full, kt * BK, (sa - 1) * a.mpad + m0);
-                            tma_load_2d(smem_u32(dst + TILE_BYTES), &maps.b, full, kt * BK,
+                            const int kx = (a.kt0 + kt) * BK;
+                            tma_load_2d(smem_u32(dst), &maps.a, full, kx, (sa - 1) * a.mpad + m0);
+                            tma_load_2d(smem_u32(dst + TILE_BYTES), &maps.b, full, kx,
                                         (L - sa - 1) * a.npad + n0);
                             armed = it + 1;
                         }
@@ -394,9 +401,17 @@ cudaError_t ozaki_gemm(cudaStream_t st, int m, int n, int k, double alpha,
     a.status = ts ? ts : (dev_now >= 0 && dev_now < kMaxDevices ? dummy_status[dev_now] : nullptr);
     if (!a.status) return cudaErrorInvalidDevice;
     dim3 grid(mpad / BM, npad / BN);
-    EGB_COUNT_LAUNCH();
-    ozaki_gemm_tc_kernel<<<grid, 192, SMEM_BYTES, st>>>(maps, a);
-    return cudaGetLastError();
+    // K segments of kOzSegK (a multiple of BK): the first applies beta, the rest add
+    for (int k0 = 0; k0 < kpad; k0 += kOzSegK) {
+        a.kt0 = k0 / BK;
+        a.kpad = min(kpad, k0 + kOzSegK);
+        a.beta = k0 == 0 ? beta : 1.0;
+        EGB_COUNT_LAUNCH();
+        ozaki_gemm_tc_kernel<<<grid, 192, SMEM_BYTES, st>>>(maps, a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace egb

@@ -314,6 +314,36 @@ __global__ void orth_defect_kernel(int k, const double *sm, unsigned long long *
     if ((threadIdx.x & 31) == 0) atomicMax(stats, (unsigned long long)__double_as_longlong(r));
 }
 
+// out[0] = max_j lam_j - w_k, the largest refined eigenvalue of the wanted block against
+// the binary32-route estimate of the first unwanted one (-inf when k = n); out[1] =
+// max(|w_0|, |w_(n-1)|, max_j |lam_j|), the scale of the spectrum. One CTA.
+__global__ void wanted_order_kernel(int n, int k, const double *lam, const double *w, double *out)
+{
+    __shared__ double smax[32], sabs[32];
+    double m = -INFINITY, a = 0.0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        m = fmax(m, lam[j]);
+        a = fmax(a, fabs(lam[j]));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smax[threadIdx.x >> 5] = m;
+        sabs[threadIdx.x >> 5] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            m = fmax(m, smax[q]);
+            a = fmax(a, sabs[q]);
+        }
+        out[0] = k < n ? m - w[k] : -INFINITY;
+        out[1] = fmax(a, fmax(fabs(w[0]), fabs(w[n - 1])));
+    }
+}
+
 __global__ void gram_diag_kernel(int k, const double *g, const double *sm, double *gd, double *sd)
 {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
@@ -372,6 +402,7 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
         // back-substitution, where a binary64 factor rounded to binary32 has the same
         // backward error (about eps_32 ||S||); the refinement works with S itself.
         CKR(check_finite<double>(st, n, n, rq.ovlp, n, w.status));
+        CKR(check_finite<double>(st, n, n, rq.ham, n, w.status));
         CKR(copy_matrix<float, double>(st, n, n, rq.ovlp, n, L, n));
         CKR(potrf<float>(st, n, L, n, INVD, WORK, w.status));
         CKR(cudaMemcpyAsync(w.status_host, w.status, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, st));
@@ -393,11 +424,17 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
             CKR(pe);
             CKR(copy_matrix<float, double>(st, n, n, L64, n, L, n));
             CKR(copy_matrix<float, double>(st, n, kTriBlock, INV64, n, INVD, n));
+            CKR(cudaMemcpyAsync(w.status_host, w.status, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, st));
+            CKR(cudaStreamSynchronize(st));
         }
+        // not positive definite in binary64 either, or a non-finite input: stop here; the
+        // caller reports the code (and the pivot) from the status words
+        if (w.status_host[ST_CODE] != 0) return ELSI_OK;
         h->have_l_prec = ELSI_PREC_FP32_REFINE;
+    } else {
+        CKR(check_finite<double>(st, n, n, rq.ham, n, w.status));
     }
     CKR(cudaEventRecord(w.ev[STAGE_STDFORM], st));
-    CKR(check_finite<double>(st, n, n, rq.ham, n, w.status));
     if (!unit) {
         CKR(copy_matrix<float, double>(st, n, n, rq.ham, n, Y, n));
         CKR(trsm_left_lower<float>(st, 0, n, n, L, n, INVD, Y, n, WORK));
@@ -535,7 +572,9 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
         CKR(cudaMemsetAsync(STATS, 0, 4 * sizeof(unsigned long long), st));
         EGB_COUNT_LAUNCH();
         orth_defect_kernel<<<grid_for((size_t)k * k), 256, 0, st>>>(k, SOO, STATS);
-        CKR(cudaMemcpyAsync(w.scal_host + 8, STATS, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        EGB_COUNT_LAUNCH();
+        wanted_order_kernel<<<1, 256, 0, st>>>(n, k, LAM, w.w, reinterpret_cast<double *>(STATS + 2));
+        CKR(cudaMemcpyAsync(w.scal_host + 8, STATS, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
         CKR(cudaStreamSynchronize(st));
     }
     h->refine_iters = iters;
@@ -545,6 +584,14 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
         return set_error(h, ELSI_ERR_NO_CONVERGENCE,
                          "refinement did not converge (max|E| %.3g, orthonormality %.3g)", emax,
                          h->orth_err);
+    // The refinement converges to the eigenpairs nearest its binary32 start. A start whose
+    // error exceeds the gaps (a standard form spoilt by a nearly singular S) can converge to
+    // a pair above the k-th: a refined wanted eigenvalue above the binary32 estimate of the
+    // first unwanted one, by more than that estimate's error, shows it.
+    if (!(w.scal_host[10] <= 1e-4 * fmax(1.0, w.scal_host[11])))
+        return set_error(h, ELSI_ERR_NO_CONVERGENCE,
+                         "refined states are not the lowest %d (max refined eigenvalue %.6g above "
+                         "the next binary32 one)", k, w.scal_host[10]);
     // eigenvalues: refined for the wanted states, binary32-route values for the rest
     EGB_COUNT_LAUNCH();
     copy_eval_kernel<<<grid_for(n), 256, 0, st>>>(n, k, LAM, w.w, w.w);

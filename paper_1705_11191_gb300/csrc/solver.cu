@@ -256,7 +256,12 @@ int run_solve(elsi_gb_handle_s *h, const SolveRequest &rq)
     CK(cudaStreamSynchronize(st));
     for (int i = 0; i < kNumStages; ++i) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, w.ev[i], w.ev[i + 1]) != cudaSuccess) ms = 0.f;
+        if (cudaEventElapsedTime(&ms, w.ev[i], w.ev[i + 1]) != cudaSuccess) {
+            // a stage the solve did not reach (an early error exit): its events were not
+            // recorded; clear the error so that the next launch check does not see it
+            (void)cudaGetLastError();
+            ms = 0.f;
+        }
         h->stage_ms[i] = ms;
     }
     const int code = w.status_host[ST_CODE];

@@ -74,3 +74,73 @@ def test_overlap_conditioning_sweep(tau):
         P, e = hd.dm_real(dev(p.h), dev(p.s))
     tol = 1e-9 if tau >= 1e-4 else 1e-8
     assert rel(P.cpu().numpy(), ref["P"]) <= tol
+
+
+def test_refined_route_not_pd_then_reuse():
+    """S not positive definite: the binary32 factorisation fails, the binary64 one fails at
+    the same pivot, and the error names it; the handle then solves a valid problem."""
+    p = ksinputs.cluster_problem(64, seed=24)
+    s = p.s.copy()
+    s[40, 40] = -1.0
+    ref = oracle.solve(p.h, p.s, p.n_state, p.n_electron)
+    with egb.Handle(p.n, p.n_state, p.n_electron) as hd:
+        hd.use_current_stream()
+        hd.set_precision(egb.PREC_FP32_REFINE)
+        hd.set_band_width(16)
+        with pytest.raises(egb.ElsiError) as e:
+            hd.dm_real(dev(p.h), dev(s))
+        assert e.value.code == 3 and "pivot 40" in str(e.value)
+        P, _ = hd.dm_real(dev(p.h), dev(p.s))
+    assert rel(P.cpu().numpy(), ref["P"]) <= 1e-9
+
+
+def test_refined_route_nonfinite_hamiltonian():
+    p = ksinputs.cluster_problem(64, seed=25)
+    h = p.h.copy()
+    h[3, 7] = np.nan
+    with egb.Handle(p.n, p.n_state, p.n_electron) as hd:
+        hd.use_current_stream()
+        hd.set_precision(egb.PREC_FP32_REFINE)
+        hd.set_band_width(16)
+        with pytest.raises(egb.ElsiError) as e:
+            hd.dm_real(dev(h), dev(p.s))
+    assert e.value.code == 4
+
+
+def test_binary64_cholesky_fallback_nearly_dependent_pair():
+    """Two basis functions i, j with overlap c = 1 - 2e-8 (lambda_min(S) = 2e-8) and no
+    overlap or coupling with the rest, H on the pair = h0 S on the pair (both of its
+    eigenvalues h0, above the whole spectrum of the rest). c rounds to 1 in binary32, so
+    the binary32 Cholesky meets a zero pivot at the later of i, j and the route factors S
+    in binary64; its binary32 standard form is still wrong on the pair by O(h0), so the
+    refinement must not return the pair's state among the wanted ones. P must equal the
+    oracle's (the pair is unoccupied and decoupled, so P is that of the rest)."""
+    sla = pytest.importorskip("scipy.linalg")
+    base = ksinputs.cluster_problem(198, seed=38)
+    h0 = float(sla.eigh(base.h, base.s, eigvals_only=True)[-1]) + 1.0
+    n, i, j = 200, 17, 150
+    c = 1.0 - 2e-8
+    assert np.float32(c) == np.float32(1.0)
+    rest = [q for q in range(n) if q not in (i, j)]
+    H = np.zeros((n, n))
+    S = np.zeros((n, n))
+    H[np.ix_(rest, rest)] = base.h
+    S[np.ix_(rest, rest)] = base.s
+    S[i, i] = S[j, j] = 1.0
+    S[i, j] = S[j, i] = c
+    H[i, i] = H[j, j] = h0
+    H[i, j] = H[j, i] = h0 * c
+    ref = oracle.solve(H, S, base.n_state, base.n_electron)
+    ref_rest = oracle.solve(base.h, base.s, base.n_state, base.n_electron)
+    # the oracle itself: P vanishes on the pair and equals the smaller problem's elsewhere
+    assert np.abs(ref["P"][[i, j], :]).max() < 1e-9
+    assert rel(ref["P"][np.ix_(rest, rest)], ref_rest["P"]) < 1e-8
+    with egb.Handle(n, base.n_state, base.n_electron) as hd:
+        hd.use_current_stream()
+        hd.set_precision(egb.PREC_FP32_REFINE)
+        hd.set_band_width(32)
+        P, e = hd.dm_real(dev(H), dev(S))
+        iters, _ = hd.refine_info()
+    assert rel(P.cpu().numpy(), ref["P"]) <= 1e-7
+    assert abs(e - ref["energy"]) <= 1e-7 * abs(ref["energy"])
+    assert iters == -1 or iters >= 1
