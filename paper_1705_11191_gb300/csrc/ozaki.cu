@@ -128,25 +128,33 @@ __global__ void ozaki_split_kernel(int V, int Vpad, int K, int Kpad, const doubl
 }
 
 // ------------------------------------------------------------------ GEMM (tcgen05)
-// One CTA per 128 x 128 tile of C, 192 threads:
+// One CTA per 128 x 128 tile of C, 320 threads:
 //   warp 0, one lane: TMA producer of the (A digit plane, B digit plane) k-tiles, 64 bf16 of
 //                     K (128 bytes, 128-byte swizzle) x 128 rows each, into a STAGES ring;
 //   warp 1, one lane: MMA issuer, tcgen05.mma kind::f16 (bf16 x bf16 -> fp32), M = N = 128,
 //                     K = 16 per instruction;
-//   warps 2..5:       epilogue, warp w owns tensor-memory lanes (rows) 32 (w mod 4) .. + 31.
+//   warps 2..9:       epilogue, warp w owns tensor-memory lanes (rows) 32 (w mod 4) .. + 31
+//                     and the tile columns 64 h .. 64 h + 63, h = (w - 2) / 4.
 // Work order: levels L = D+1 down to 2 (smallest contributions first), chunks of 256 along
 // K, pairs (s, L - s), k-tiles. Each chunk's sum over its pairs and k-tiles goes to one of
-// two tensor-memory accumulators: the products are integers and the sum stays below 2^24,
-// so the accumulation is exact whatever its rounding. The epilogue converts each chunk to
-// int32 and adds it in registers (exact); at the end of a level it adds
-// alpha 2^(e_i + f_j - 7L) times the level sum to C in binary64.
+// two tensor-memory accumulators (columns 0..127 and 128..255): the products are integers
+// and the sum stays below 2^24, so the accumulation is exact whatever its rounding. The
+// epilogue converts each chunk to int32 and adds it in registers (exact); at the end of a
+// level it adds alpha 2^(e_i + f_j - 7L) times the level sum to a binary64 running sum of
+// the tile kept in tensor memory (columns 256..511, the two 32-bit halves of column j's
+// value at 256 + 2j and 257 + 2j), and C is written once, after the last level. (Adding
+// each level to C in global memory instead costs a 256 KB read-modify-write per tile and
+// level, which stalls the MMA issuer once it has filled the second accumulator and
+// dominates products with a short K.)
 namespace oztc {
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 5;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 7;
 constexpr int CHUNK_TILES = 256 / BK;         // k-tiles per exact chunk
 constexpr int TILE_BYTES = BM * BK * 2;       // 16 KB
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;   // A tile + B tile
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int TMEM_COLS = 2 * BN;
+constexpr int TMEM_COLS = 4 * BN;  // two accumulators + the binary64 running sum
+constexpr int EPI_WARPS = 8, CW = BN / 2;  // epilogue warps; columns per epilogue warp
+constexpr int THREADS = 32 * (2 + EPI_WARPS);
 
 struct Maps {
     CUtensorMap a, b;  // planes as (D * Mpad) x Kpad and (D * Npad) x Kpad bf16 matrices
@@ -163,7 +171,15 @@ struct Args {
 };
 }  // namespace oztc
 
-__global__ void __launch_bounds__(192, 1)
+// x 2^e: a multiplication by a power of two built from its bit pattern where 2^e is a normal
+// number (exact, like ldexp), ldexp elsewhere.
+__device__ __forceinline__ double scale2(double x, int e)
+{
+    if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
+    return ldexp(x, e);
+}
+
+__global__ void __launch_bounds__(oztc::THREADS, 1)
 ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a)
 {
     using namespace oztc;
@@ -186,8 +202,8 @@ ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a
 
     if (tid == 0) {
         for (int q = 0; q < 2 * STAGES + 2; ++q) mbar_init(smem_u32(&bars[q]), 1);
-        mbar_init(acce0, 4);
-        mbar_init(acce0 + 8, 4);
+        mbar_init(acce0, EPI_WARPS);
+        mbar_init(acce0 + 8, EPI_WARPS);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         aborted = 0;
     }
@@ -271,18 +287,23 @@ ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a
             }
         }
     } else {
-        const int quarter = warp & 3;
+        // tensor-memory loads and stores are warp-collective: every lane runs them (rows past
+        // m only skip their global-memory accesses) and the wait results are made uniform
+        const int quarter = warp & 3, c0 = ((warp - 2) >> 2) * CW;  // rows, first column
         const int row = m0 + quarter * 32 + lane;
-        const int er = (row < a.m_real) ? a.ea[row] : 0;
-        int iacc[BN];
+        const bool row_in = row < a.m_real;
+        const int er = row_in ? a.ea[row] : 0;
+        const unsigned tlane = tmem + ((unsigned)(quarter * 32) << 16);
+        const unsigned tsum = tlane + 2 * BN + 2 * c0;
+        int iacc[CW];
         bool ok = true;
         int g = 0;
         for (int L = a.digits + 1; L >= 2 && ok; --L) {
 #pragma unroll
-            for (int j = 0; j < BN; ++j) iacc[j] = 0;
+            for (int j = 0; j < CW; ++j) iacc[j] = 0;
             for (int c = 0; c < nch; ++c, ++g) {
                 const int bsel = g & 1;
-                ok = mbar_wait(accf0 + 8 * bsel, (g >> 1) & 1);
+                ok = __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * bsel, (g >> 1) & 1));
                 if (!ok) {
                     if (lane == 0) {
                         report_error(a.status, ELSI_ERR_TIMEOUT, 14);
@@ -292,9 +313,9 @@ ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a
                 }
                 tc_fence_after();
 #pragma unroll
-                for (int q = 0; q < BN / 32; ++q) {
+                for (int q = 0; q < CW / 32; ++q) {
                     float v[32];
-                    tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + bsel * BN + q * 32, v);
+                    tmem_ld32(tlane + bsel * BN + c0 + q * 32, v);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) iacc[q * 32 + j] += __float2int_rn(v[j]);
                 }
@@ -302,26 +323,45 @@ ozaki_gemm_tc_kernel(const __grid_constant__ oztc::Maps maps, const oztc::Args a
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acce0 + 8 * bsel);
             }
-            if (!ok || row >= a.m_real) continue;
-            // C (+)= alpha 2^(e_i + f_j - 7L) level sum, 16 columns at a time
+            if (!ok) break;
+            // running sum += alpha 2^(e_i + f_j - 7L) level sum, 16 columns at a time
             const bool firstL = (L == a.digits + 1);
-            double *crow = a.C + (size_t)row;
 #pragma unroll
-            for (int q = 0; q < BN / 16; ++q) {
+            for (int q = 0; q < CW / 16; ++q) {
+                unsigned w[32];
+                if (!firstL) tmem_ld32_u(tsum + q * 32, w);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + q * 16 + j;
+                    const int ec = col < a.n_real ? a.eb[col] : 0;
+                    const double val = a.alpha * scale2((double)iacc[q * 16 + j], er + ec - kOzBits * L);
+                    const double sum = firstL ? val : __hiloint2double((int)w[2 * j + 1], (int)w[2 * j]) + val;
+                    w[2 * j] = (unsigned)__double2loint(sum);
+                    w[2 * j + 1] = (unsigned)__double2hiint(sum);
+                }
+                tmem_st32_u(tsum + q * 32, w);
+            }
+        }
+        if (ok) {
+            // C = beta C + running sum, 16 columns at a time (the loads of C first)
+            double *crow = a.C + (size_t)row;
+#pragma unroll 1
+            for (int q = 0; q < CW / 16; ++q) {
+                unsigned w[32];
+                tmem_ld32_u(tsum + q * 32, w);
                 double cv[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + q * 16 + j;
-                    const bool in = col < a.n_real && (!a.uplo || row >= col);
-                    cv[j] = (in && (!firstL || a.beta != 0.0)) ? crow[(size_t)col * a.ldc] : 0.0;
+                    const int col = n0 + c0 + q * 16 + j;
+                    const bool in = row_in && col < a.n_real && (!a.uplo || row >= col);
+                    cv[j] = (in && a.beta != 0.0) ? crow[(size_t)col * a.ldc] : 0.0;
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + q * 16 + j;
-                    if (col < a.n_real && (!a.uplo || row >= col)) {
-                        const double val =
-                            a.alpha * ldexp((double)iacc[q * 16 + j], er + a.eb[col] - kOzBits * L);
-                        crow[(size_t)col * a.ldc] = firstL ? fma(a.beta, cv[j], val) : cv[j] + val;
+                    const int col = n0 + c0 + q * 16 + j;
+                    if (row_in && col < a.n_real && (!a.uplo || row >= col)) {
+                        const double sum = __hiloint2double((int)w[2 * j + 1], (int)w[2 * j]);
+                        crow[(size_t)col * a.ldc] = a.beta != 0.0 ? fma(a.beta, cv[j], sum) : sum;
                     }
                 }
             }
@@ -407,7 +447,7 @@ cudaError_t ozaki_gemm(cudaStream_t st, int m, int n, int k, double alpha,
         a.kpad = min(kpad, k0 + kOzSegK);
         a.beta = k0 == 0 ? beta : 1.0;
         EGB_COUNT_LAUNCH();
-        ozaki_gemm_tc_kernel<<<grid, 192, SMEM_BYTES, st>>>(maps, a);
+        ozaki_gemm_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(maps, a);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

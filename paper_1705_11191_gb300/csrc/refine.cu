@@ -518,13 +518,13 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
         else CKR(cudaMemcpyAsync(YS, XO, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
         CKR(ozaki_split(st, k, n, YH, n, 1, nullptr, nullptr, YHDG, eYH));
         CKR(ozaki_split(st, k, n, YS, n, 1, nullptr, nullptr, YSDG, eYS));
-        CKR(ozaki_gemm(st, k, k, n, 1.0, XDG, eX, YHDG, eYH, 0.0, GOO, k, 0, digits));
-        CKR(ozaki_gemm(st, k, k, n, 1.0, XDG, eX, YSDG, eYS, 0.0, SOO, k, 0, digits));
-        // X^T H X and X^T S X are symmetric; rounding of the two products is not, and an
+        // X^T H X and X^T S X are symmetric; the rounding of a full product is not, and an
         // antisymmetric error would enter E_ij + E_ji (the re-orthonormalisation) divided
-        // by lambda_j - lambda_i. Use the symmetric parts.
-        CKR(symmetrize<double>(st, k, GOO, k));
-        CKR(symmetrize<double>(st, k, SOO, k));
+        // by lambda_j - lambda_i. Form the lower triangles (half the work) and mirror them.
+        CKR(ozaki_gemm(st, k, k, n, 1.0, XDG, eX, YHDG, eYH, 0.0, GOO, k, 1, digits));
+        CKR(ozaki_gemm(st, k, k, n, 1.0, XDG, eX, YSDG, eYS, 0.0, SOO, k, 1, digits));
+        CKR(mirror_lower<double>(st, k, GOO, k));
+        CKR(mirror_lower<double>(st, k, SOO, k));
         cluster_scan_kernel<<<1, 1, 0, st>>>(k, GOO, SOO, delta, CID, CSZ);
         cluster_rr_kernel<<<k, 32, 0, st>>>(k, GOO, SOO, CID, CSZ, QBUF);
         rotate_cols_kernel<<<dim3(k, ceil_div(n, 256)), 256, 0, st>>>(n, k, CID, CSZ, QBUF, XO, YH, YS);
