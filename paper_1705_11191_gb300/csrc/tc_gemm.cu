@@ -5,17 +5,19 @@
 // term is below binary32 rounding). This is the binary32 GEMM of the reduction and the
 // back-transformations of the binary32 route.
 //
-// Structure of one CTA (192 threads, one 128 x 128 tile of C):
+// Structure of one CTA (320 threads; persistent over 128 x 128 tiles of C):
 //   warp 0, one lane : TMA producer. Loads the K-major hi and lo tiles of A and B (32 fp32 of
 //                      K = 128 bytes per row, 128-byte swizzle) into a 3-stage ring, one
 //                      mbarrier per stage with the transaction byte count;
 //   warp 1, one lane : MMA issuer. tcgen05.mma kind::tf32, M = 128, N = 128, K = 8 per
 //                      instruction, accumulator in tensor memory (128 lanes x 128 columns);
 //                      tcgen05.commit frees a stage when its MMAs have read it;
-//   warps 2-5        : epilogue: sum the K chunks of the two tensor-memory accumulators
-//                      (tcgen05.ld, 32 rows per warp) in registers, then C = alpha acc +
-//                      beta C with coalesced column-major stores; warp 2 allocates and
-//                      frees the tensor memory.
+//   warps 2-9        : epilogue: warp w owns rows 32 (w mod 4) .. + 31 and columns
+//                      64 h .. 64 h + 63 (h = (w - 2) / 4) of the tile. It sums the K
+//                      chunks of the two tensor-memory accumulators (tcgen05.ld) in
+//                      registers, then loads its part of C (beta != 0; 32 columns in flight
+//                      at once) and writes C = alpha acc + beta C with coalesced
+//                      column-major stores; warp 2 allocates and frees the tensor memory.
 // Every wait is bounded; on expiry the kernel records ELSI_ERR_TIMEOUT and finishes without
 // further waits on the pipeline (after a bounded wait for its own TMA copies in flight).
 #include <cuda.h>
@@ -37,6 +39,8 @@ constexpr int TILE_BYTES = BM * BK * 4;  // 16 KB (BN == BM)
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int TMEM_COLS = 4 * BN;  // two buffers x (hi*hi sum, cross-term sum)
+constexpr int EPI_WARPS = 8, CW = BN / 2;  // epilogue warps; columns per epilogue warp
+constexpr int THREADS = 32 * (2 + EPI_WARPS);
 
 __device__ __forceinline__ void mma_tf32(unsigned tmem_d, unsigned long long a, unsigned long long b,
                                          unsigned idesc, unsigned accum)
@@ -53,7 +57,7 @@ struct Maps {
 };
 
 
-// Warps: 0 = TMA producer (one lane), 1 = MMA issuer (one lane), 2..5 = epilogue (warp w
+// Warps: 0 = TMA producer (one lane), 1 = MMA issuer (one lane), 2..9 = epilogue (warp w
 // reads tensor-memory lanes 32 (w mod 4) .. + 31, i.e. those rows of the tile). K is
 // accumulated in chunks of CH k-tiles in one of two tensor-memory buffers, each holding the
 // hi*hi sum and the (2^-11 times smaller) cross-term sum separately; the epilogue warps add
@@ -75,7 +79,7 @@ __device__ __forceinline__ bool tile_of(int t, int tiles_m, int uplo, int *m0, i
     return !(uplo && *m0 + BM - 1 < *n0);  // false: strictly above the diagonal
 }
 
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(THREADS, 1)
 gemm_tf32x3_kernel(const __grid_constant__ Maps maps, int m, int n, int kp, float alpha,
                    float beta, float *__restrict__ C, int ldc, int uplo, int *status)
 {
@@ -96,8 +100,8 @@ gemm_tf32x3_kernel(const __grid_constant__ Maps maps, int m, int n, int kp, floa
 
     if (tid == 0) {
         for (int s = 0; s < 2 * STAGES + 2; ++s) mbar_init(smem_u32(&bars[s]), 1);
-        mbar_init(acce0, 4);
-        mbar_init(acce0 + 8, 4);
+        mbar_init(acce0, EPI_WARPS);
+        mbar_init(acce0 + 8, EPI_WARPS);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         aborted = 0;
     }
@@ -186,18 +190,23 @@ gemm_tf32x3_kernel(const __grid_constant__ Maps maps, int m, int n, int kp, floa
             }
         }
     } else {
-        const int quarter = warp & 3;
+        // tensor-memory loads are warp-collective: every lane runs them (rows past m only
+        // skip their global-memory accesses) and the wait results are made uniform
+        const int quarter = warp & 3, c0 = ((warp - 2) >> 2) * CW;
         bool ok = true;
         int gbase = 0;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             int m0, n0;
             if (!tile_of(t, tiles_m, uplo, &m0, &n0)) continue;
-            float acc[BN];
+            const int row = m0 + quarter * 32 + lane;
+            const bool row_in = row < m;
+            float *crow = C + (size_t)row;
+            float acc[CW];
 #pragma unroll
-            for (int j = 0; j < BN; ++j) acc[j] = 0.0f;
+            for (int j = 0; j < CW; ++j) acc[j] = 0.0f;
             for (int c = 0; c < nchunk && ok; ++c) {
                 const int g = gbase + c, bsel = g & 1;
-                ok = mbar_wait(accf0 + 8 * bsel, (g >> 1) & 1);
+                ok = __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * bsel, (g >> 1) & 1));
                 if (!ok) {
                     if (lane == 0) {
                         report_error(status, ELSI_ERR_TIMEOUT, 3);
@@ -207,9 +216,10 @@ gemm_tf32x3_kernel(const __grid_constant__ Maps maps, int m, int n, int kp, floa
                 }
                 tc_fence_after();
 #pragma unroll
-                for (int q = 0; q < BN / 32; ++q) {
+                for (int q = 0; q < CW / 32; ++q) {
                     float v[32];
-                    const unsigned ta = tmem + ((unsigned)(quarter * 32) << 16) + bsel * 2 * BN + q * 32;
+                    const unsigned ta =
+                        tmem + ((unsigned)(quarter * 32) << 16) + bsel * 2 * BN + c0 + q * 32;
                     tmem_ld32(ta + BN, v);  // cross terms
 #pragma unroll
                     for (int j = 0; j < 32; ++j) acc[q * 32 + j] += v[j];
@@ -222,25 +232,24 @@ gemm_tf32x3_kernel(const __grid_constant__ Maps maps, int m, int n, int kp, floa
                 if (lane == 0) mbar_arrive(acce0 + 8 * bsel);
             }
             gbase += nchunk;
-            const int row = m0 + quarter * 32 + lane;
-            if (ok && row < m) {
-                // 16 columns at a time: all loads of C first (independent, in flight
-                // together), then the stores; each column is one 128-byte line per warp.
-                float *crow = C + (size_t)row;
+            if (ok && row_in) {
+                // 32 loads of C at a time (one 128-byte line per column and warp, 32 KB in
+                // flight per CTA), then their stores
 #pragma unroll
-                for (int q = 0; q < BN / 16; ++q) {
-                    float cv[16];
+                for (int h = 0; h < CW / 32; ++h) {
+                    float cv[32];
+                    float *cp = crow + (size_t)(n0 + c0 + h * 32) * ldc;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = n0 + q * 16 + j;
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + h * 32 + j;
                         const bool in = col < n && (!uplo || row >= col);
-                        cv[j] = (beta != 0.0f && in) ? crow[(size_t)col * ldc] : 0.0f;
+                        cv[j] = (beta != 0.0f && in) ? cp[(size_t)j * ldc] : 0.0f;
                     }
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = n0 + q * 16 + j;
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = n0 + c0 + h * 32 + j;
                         if (col < n && (!uplo || row >= col))
-                            crow[(size_t)col * ldc] = alpha * acc[q * 16 + j] + beta * cv[j];
+                            cp[(size_t)j * ldc] = alpha * acc[h * 32 + j] + beta * cv[j];
                     }
                 }
             }
@@ -365,7 +374,7 @@ cudaError_t tc_gemm_f32_parts(cudaStream_t st, int m, int n, int nparts, const T
     const long long ntiles = (long long)((m + BM - 1) / BM) * ((n + BN - 1) / BN);
     const int grid = (int)(ntiles < nsm ? ntiles : nsm);
     EGB_COUNT_LAUNCH();
-    gemm_tf32x3_kernel<<<grid, 192, SMEM_BYTES, st>>>(maps, m, n, kp, alpha, beta, C, ldc, uplo, status);
+    gemm_tf32x3_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(maps, m, n, kp, alpha, beta, C, ldc, uplo, status);
     return cudaGetLastError();
 }
 
