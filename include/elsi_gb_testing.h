@@ -49,6 +49,21 @@ size_t elsi_gb_q2_work(int n, int b);
 int elsi_gb_q2_apply_f32(int n, int b, const float *v2, const float *tau2, int k, float *z, int ldz,
                          float *work, size_t work_elems, int *status, void *stream);
 
+/*
+ * elsi_gb_symm_tall_f32: X (m x nv, column-major, ldx) = A V for a symmetric m x m binary32
+ *   matrix A (full column-major storage, lda a multiple of 4, A 16-byte aligned) and an
+ *   m x nv panel V (ldv), 1 <= nv <= 64: the product A22 V of the two-sided update of the
+ *   full-to-band reduction (Eq. 11, sec. 3.1), binary32 accuracy on the tcgen05 tensor
+ *   cores, A read once (split into TF32 hi/lo parts in shared memory). Only the symmetry of
+ *   A is used: column i of A stands for row i. work: device scratch of
+ *   elsi_gb_symm_tall_f32_work(m) floats (16-byte aligned); status: device int[8], zeroed
+ *   by the caller (ELSI_ERR_TIMEOUT if a pipeline wait expired). Enqueued on stream (may
+ *   be NULL). Returns 0, ELSI_ERR_ARG for bad sizes, alignment or scratch, ELSI_ERR_CUDA.
+ */
+size_t elsi_gb_symm_tall_f32_work(int m);
+int elsi_gb_symm_tall_f32(int m, int nv, const float *A, int lda, const float *V, int ldv, float *X,
+                          int ldx, float *work, size_t work_elems, int *status, void *stream);
+
 size_t elsi_gb_gemm_f32_work(int m, int n, int k);
 int elsi_gb_gemm_f32(int ta, int tb, int m, int n, int k, float alpha, const float *A, int lda,
                      const float *B, int ldb, float beta, float *C, int ldc, int uplo,

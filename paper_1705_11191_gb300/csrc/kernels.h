@@ -20,6 +20,14 @@ cudaError_t gemm(cudaStream_t st, int ta, int tb, int m, int n, int k, T alpha,
 // tc_gemm.cu). work: tc_gemm_work_elems(m, n, k) floats, 16-byte aligned. Returns
 // cudaErrorNotSupported when it cannot run (scratch too small, no tensor-map encoder).
 size_t tc_gemm_work_elems(int m, int n, int k);
+
+// X (m x nv, ldx) = A V for a symmetric m x m binary32 A (full storage, lda a multiple of 4,
+// 16-byte aligned) and an m x nv panel V (nv <= 64), binary32 accuracy on the tensor cores
+// (symm_tall.cu). work: symm_tall_work_elems(m) floats, 16-byte aligned. Returns
+// cudaErrorNotSupported when the operands do not fit its constraints.
+size_t symm_tall_work_elems(int m);
+cudaError_t symm_tall_f32(cudaStream_t st, int m, int nv, const float *A, int lda, const float *V,
+                          int ldv, float *X, int ldx, float *work, size_t work_elems, int *status);
 // Sum of products over K pieces: C = alpha * sum_i op(A_i) op(B_i) + beta * C, piece i of
 // width k (the same for A_i and B_i), op(A_i) m x k (trans = 0: p[r + q ld], 1: p[q + r ld]),
 // op(B_i) k x n (trans = 0: p[q + c ld], 1: p[c + q ld]).

@@ -452,8 +452,23 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         T *W = work + (size_t)n * b;      // m x b
         T *Y = work + (size_t)2 * n * b;  // b x b
         T *Z = Y + (size_t)b * b;         // b x b
-        // X = A22 V
-        if ((e = gemm<T>(st, 0, 0, m, bw, m, T(1), A22, lda, V, n, T(0), W, m)) != cudaSuccess) return e;
+        // X = A22 V (binary32: the symmetric panel product that streams A22 once)
+        bool xdone = false;
+        if constexpr (sizeof(T) == 4) {
+            float *tw;
+            size_t te;
+            int *ts;
+            if (tc_scratch(&tw, &te, &ts)) {
+                e = symm_tall_f32(st, m, bw, (const float *)A22, lda, (const float *)V, n, (float *)W, m,
+                                  tw, te, ts);
+                if (e != cudaErrorNotSupported) {
+                    if (e != cudaSuccess) return e;
+                    xdone = true;
+                }
+            }
+        }
+        if (!xdone && (e = gemm<T>(st, 0, 0, m, bw, m, T(1), A22, lda, V, n, T(0), W, m)) != cudaSuccess)
+            return e;
         if (ceil_div(m, kWRows) + 1 <= max_g) {
             // X = (A22 V) T, W = X - 1/2 V (T^T (V^T X)); the per-block partials of V^T X
             // and their sum use the (now idle) Gram scratch of the panel factorisation
