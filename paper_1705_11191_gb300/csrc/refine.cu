@@ -460,8 +460,11 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     }
     CKR(cudaEventRecord(w.ev[STAGE_TRIDIAG], st));
     // binary32-route eigenvalues: the wanted ones are recomputed by the refinement and the
-    // rest are reported at the accuracy of this route, so 1e-10 ||T|| suffices
-    CKR(stebz(st, n, w.d, w.e, n, w.w, w.status, 1e-10));
+    // rest are reported at the accuracy of this route. T itself carries the binary32
+    // rounding of the reduction (about 6e-8 ||T||), so bisection to 1e-8 ||T|| changes
+    // neither the eigenvalues nor, through the twisted factorisations, the eigenvectors
+    // beyond that level.
+    CKR(stebz(st, n, w.d, w.e, n, w.w, w.status, 1e-8));
     // eigenvector scratch (3 n^2 + n binary64 values) in the digit-plane buffer, free here
     CKR(stein<float>(st, n, w.d, w.e, n, w.w, X32, n, reinterpret_cast<double *>(w.oz), w.status));
     CKR(cudaEventRecord(w.ev[STAGE_Q2], st));
