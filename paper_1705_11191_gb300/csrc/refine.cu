@@ -510,10 +510,9 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
 
     // products, cluster Rayleigh-Ritz rotation and the Rayleigh quotients of the
     // current X_o (steps shared by every iteration and the final polish). digits: digit
-    // planes of the binary64-accurate products; an iteration only needs its products
-    // accurate to well below the error it corrects, so the first iterations (errors of
-    // about 1e-3 and 1e-5 in X) use 4 and 5 of the 7 digits (10 and 15 digit products
-    // instead of 28; truncation about 2^-35 and 2^-42 relative), the later ones all 7.
+    // planes of the binary64-accurate products (D digits: D (D + 1) / 2 digit products,
+    // truncation about 2^(-7 D) relative); the first iterations, which correct errors of
+    // about 1e-3, need fewer than the later ones and the final polish (see the loop).
     auto products_and_rr = [&](int digits) -> int {
         CKR(ozaki_split(st, k, n, XO, n, 1, nullptr, nullptr, XDG, eX));
         CKR(ozaki_gemm(st, n, k, n, 1.0, HDG, eH, XDG, eX, 0.0, YH, n, 0, digits));
@@ -545,7 +544,14 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     int iters = 0;
     double emax = 1.0;
     for (int it = 0; it < h->refine_max_iter; ++it) {
-        int rc = products_and_rr(it == 0 ? 4 : (it == 1 ? 5 : kOzDigits));
+        // digit planes of this iteration's products: 4 and 5 in the first two iterations
+        // (binary32 start, errors of about 1e-3), 7 from the third on. The corrections of
+        // the states next to the wanted/unwanted boundary are divided by their gap, which
+        // can be far below the cluster threshold: with 5 digits in the third iteration
+        // max|E| stalls near 6e-4 on the 3D-cluster problem at n = 16384 (the binary64
+        // fallback follows), with 7 it reaches 9e-6 and then 1.4e-9.
+        const int digits = it == 0 ? 4 : (it == 1 ? 5 : kOzDigits);
+        int rc = products_and_rr(digits);
         if (rc) return rc;
         // M = Xu^T R_o in binary32
         if (n > k)
@@ -564,8 +570,8 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
         emax = w.scal_host[8];
         ++iters;
         if (verbose)
-            fprintf(stderr, "[elsi-gb] refine iteration %d: max|E| %.3e, max|R_oo| %.3e\n", iters, emax,
-                    w.scal_host[9]);
+            fprintf(stderr, "[elsi-gb] refine iteration %d (%d digits): max|E| %.3e, max|R_oo| %.3e\n", iters,
+                    digits, emax, w.scal_host[9]);
         if (emax < 1e-12) break;
     }
     // final polish: Rayleigh-Ritz inside clusters, Rayleigh quotients, orthonormality
