@@ -136,6 +136,10 @@ template <typename T>
 __device__ __forceinline__ T ldg_l2(const T *p) { return __ldcg(p); }
 
 
+// Columns of a b x b tile per thread in the element loops (row ti = tid mod 64, columns
+// tc, tc + 4, ..., tc = tid / 64; 256 threads, b <= 64).
+constexpr int kChaseCols = 16;
+
 // One (sweep j, step t) task; all threads of the CTA take part. The b x b tiles use the
 // leading dimension b + 8, which makes the four-lanes-per-row dot products
 // conflict-free in shared memory.
@@ -158,9 +162,21 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
         const int L = min(b, n - 1 - j);
         const int r0 = j + 1;
         for (int i = tid; i < b; i += nt) vnew[i] = (i < L) ? ldg_l2(band + (size_t)(1 + i) + (size_t)j * ldb) : T(0);
-        // D = A[j+1 .. j+L]^2: lower triangle from the band, upper by symmetry
-        if (ti < L)
-            for (int c = tc; c <= ti; c += 4) D[ti + c * ld] = ldg_l2(band + (size_t)(ti - c) + (size_t)(r0 + c) * ldb);
+        // D = A[j+1 .. j+L]^2: lower triangle from the band, upper by symmetry (all loads of
+        // a thread in flight together)
+        {
+            T dr[kChaseCols];
+#pragma unroll
+            for (int q = 0; q < kChaseCols; ++q) {
+                const int c = tc + 4 * q;
+                dr[q] = (ti < L && c <= ti) ? ldg_l2(band + (size_t)(ti - c) + (size_t)(r0 + c) * ldb) : T(0);
+            }
+#pragma unroll
+            for (int q = 0; q < kChaseCols; ++q) {
+                const int c = tc + 4 * q;
+                if (ti < L && c <= ti) D[ti + c * ld] = dr[q];
+            }
+        }
         __syncthreads();
         if (ti < L)
             for (int c = ti + 1 + tc; c < L; c += 4) D[ti + c * ld] = D[c + ti * ld];
@@ -184,12 +200,25 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     for (int i = tid; i < b; i += nt) vprev[i] = ldg_l2(v2 + pslot * b + i);
     const T taup = ldg_l2(tau2 + pslot);
     // X = A[r .. r+L-1, cb .. cb+b-1]  (all strictly below the diagonal, distance 1..2b-1)
-    if (ti < L)
-        for (int c = tc; c < b; c += 4) X[ti + c * ld] = ldg_l2(band + (size_t)(r + ti - (cb + c)) + (size_t)(cb + c) * ldb);
-    // D = A[r .. r+L-1]^2 (read now: the task's window is not touched by anyone else);
-    // lower triangle from the band, upper by symmetry
-    if (ti < L)
-        for (int c = tc; c <= ti; c += 4) D[ti + c * ld] = ldg_l2(band + (size_t)(ti - c) + (size_t)(r + c) * ldb);
+    // and D = A[r .. r+L-1]^2 (read now: the task's window is not touched by anyone else;
+    // lower triangle from the band, upper by symmetry). Every load of a thread is issued
+    // before the first store to shared memory, so that the (up to 32) L2 round trips of a
+    // thread overlap instead of following one another.
+    {
+        T xr[kChaseCols], dr[kChaseCols];
+#pragma unroll
+        for (int q = 0; q < kChaseCols; ++q) {
+            const int c = tc + 4 * q;
+            xr[q] = (ti < L && c < b) ? ldg_l2(band + (size_t)(r + ti - (cb + c)) + (size_t)(cb + c) * ldb) : T(0);
+            dr[q] = (ti < L && c <= ti) ? ldg_l2(band + (size_t)(ti - c) + (size_t)(r + c) * ldb) : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < kChaseCols; ++q) {
+            const int c = tc + 4 * q;
+            if (ti < L && c < b) X[ti + c * ld] = xr[q];
+            if (ti < L && c <= ti) D[ti + c * ld] = dr[q];
+        }
+    }
     __syncthreads();
     if (ti < L)
         for (int c = ti + 1 + tc; c < L; c += 4) D[ti + c * ld] = D[c + ti * ld];
