@@ -25,7 +25,7 @@ struct PanelArgs {
     double *alpha;           // 2 x 64: row j of the panel (by column parity)
     double *wpart;           // 2 x gstride x 64 partial dot products (by column parity)
     int gstride;             // >= G
-    double *gram;            // G x bw x bw partial Gram matrices
+    double *gram;            // scratch of the W kernels (not used by the panel kernel)
     int *status;
     long long spin_limit;    // polls of a grid-barrier wait before ELSI_ERR_TIMEOUT
 };
@@ -47,11 +47,25 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
     const int row0 = g * R;
     const int nrow = max(0, min(a.m - row0, R));
     const int tc = tid & 63, tr = tid >> 6;  // 64 column lanes x 4 row lanes
+    // T of the compact-WY form, column by column (CTA 0), after the panel rows
+    double *tloc = reinterpret_cast<double *>(smem_raw + (((size_t)R * bwp * sizeof(T) + 15) & ~(size_t)15));
 
-    for (int e = tid; e < R * bw; e += blockDim.x) {
-        int i = e % R, c = e / R;
-        Ploc[i * bwp + c] = (i < nrow) ? P[(size_t)(row0 + i) + (size_t)c * a.lda] : T(0);
+    // the panel rows of this CTA, 16 loads of a thread in flight at a time
+    for (int e0 = 0; e0 < R * bw; e0 += 16 * 256) {
+        T v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = e0 + u * 256 + tid, i = e % R, c = e / R;
+            v[u] = (e < R * bw && i < nrow) ? P[(size_t)(row0 + i) + (size_t)c * a.lda] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = e0 + u * 256 + tid, i = e % R, c = e / R;
+            if (e < R * bw) Ploc[i * bwp + c] = v[u];
+        }
     }
+    if (g == 0)
+        for (int e = tid; e < 64 * 64; e += blockDim.x) tloc[e] = 0.0;
     __syncthreads();
 
     const int nref = min(bw, a.m);
@@ -61,7 +75,10 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
     // row j publishes that row. After it, every CTA forms the same reflector
     // v = [1; x scl] and w_c = v . P_c = P[j][c] + scl d_c, and updates its rows. The
     // published values alternate between two buffers by column parity: a CTA can be at
-    // most one column ahead of another.
+    // most one column ahead of another. The free slots c < j - 1 of the same exchange
+    // carry the partial Gram column G[c][j-1] = v_c . v_(j-1) of the finished reflectors,
+    // from which CTA 0 forms column j - 1 of T (forward recurrence) while the others
+    // update their rows.
     for (int j = 0; j < nref; ++j) {
         const int par = j & 1;
         double *part = a.part + (size_t)par * a.gstride;              // [G]
@@ -75,6 +92,13 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             if (c > j && c < bw)
                 for (int i = tr; i < nrow; i += 4)
                     if (row0 + i > j) s = fma(Ploc[i * bwp + j], Ploc[i * bwp + c], s);
+            if (c < j - 1)  // v_c . v_(j-1) over the rows >= j - 1 (v_c is zero above c)
+                for (int i = tr; i < nrow; i += 4) {
+                    const int gi = row0 + i;
+                    if (gi < j - 1) continue;
+                    const T vj = (gi == j - 1) ? T(1) : Ploc[i * bwp + j - 1];
+                    s = fma(Ploc[i * bwp + c], vj, s);
+                }
             colpart[tr][tc] = (double)s;
             double sst = block_sum((double)ss, red);  // also orders colpart
             if (tid < bw)
@@ -97,7 +121,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             // before they are summed
             // (up to 64 CTAs: all 16 loads of a thread in flight at once)
             double dv = 0.0;
-            if (tc > j && tc < bw) {
+            if ((tc > j && tc < bw) || tc < j - 1) {
                 double acc[16];
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
@@ -132,6 +156,16 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             __syncthreads();
         }
         const double beta = refl[0], tau = refl[1], scl = refl[2];
+        // column j - 1 of T: T[c][j-1] = -tau_(j-1) sum_(c <= q < j-1) T[c][q] G[q][j-1]
+        if (g == 0 && j >= 1) {
+            if (tid < j - 1) {
+                double acc = 0.0;
+                for (int q = tid; q < j - 1; ++q) acc += tloc[tid + q * 64] * wsum[q];
+                tloc[tid + (j - 1) * 64] = -tau_s[j - 1] * acc;
+            }
+            if (tid == 0) tloc[(j - 1) + (j - 1) * 64] = tau_s[j - 1];
+            __syncthreads();
+        }
         // w_c = P[j][c] + scl d_c; stored pre-multiplied by tau
         if (tid > j && tid < bw) wsum[tid] = tau * (__ldcg(prow + tid) + scl * wsum[tid]);
         __syncthreads();
@@ -170,56 +204,57 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
         T vv = (c >= nref) ? T(0) : ((gi > c) ? pv : ((gi == c) ? T(1) : T(0)));
         V[(size_t)gi + (size_t)c * a.ldv] = vv;
     }
-    // ---- Gram matrix V^T V (partial per CTA), then T by the forward recurrence
-    for (int e = tid; e < bw * bw; e += blockDim.x) {
-        int r = e % bw, c = e / bw;
+    // ---- the last column of T: partial Gram column G[c][nref-1] (c < nref - 1) through the
+    //      buffer of the next parity, one more barrier, then CTA 0 sums and finishes T
+    const int jl = nref - 1;
+    {
+        double *dpart = a.wpart + (size_t)(nref & 1) * a.gstride * 64;
         T s = T(0);
-        if (r < nref && c < nref && r <= c) {
-            for (int i = 0; i < nrow; ++i) {
-                int gi = row0 + i;
-                T vr = (gi > r) ? Ploc[i * bwp + r] : (gi == r ? T(1) : T(0));
-                T vc = (gi > c) ? Ploc[i * bwp + c] : (gi == c ? T(1) : T(0));
-                s = fma(vr, vc, s);
+        if (tc < jl)
+            for (int i = tr; i < nrow; i += 4) {
+                const int gi = row0 + i;
+                if (gi < jl) continue;
+                const T vj = (gi == jl) ? T(1) : Ploc[i * bwp + jl];
+                s = fma(Ploc[i * bwp + tc], vj, s);
             }
-        }
-        a.gram[(size_t)g * bw * bw + e] = (double)s;
+        colpart[tr][tc] = (double)s;
+        __syncthreads();
+        if (tid < bw) dpart[(size_t)g * 64 + tid] = colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
     }
     if (!grid_barrier(a.count, (unsigned)G * (unsigned)(nref + 1), a.status, a.spin_limit)) return;
     if (g != 0) return;
-    double *gsum = reinterpret_cast<double *>(smem_raw);  // reuse: bw x bw (fits: R*bwp*sizeof(T) >= ...)
-    double *tloc = gsum + bw * bw;
-    // (L2-coherent loads of the partials written before the barrier; 8 in flight per
-    // thread)
-    for (int e = tid; e < bw * bw; e += blockDim.x) {
-        double s = 0.0;
-        if (e % bw < e / bw) {  // only G[r][c], r < c, enters the recurrence below
-            double acc[8];
-            int q = 0;
-            for (; q + 8 <= G; q += 8) {
+    {
+        const double *dpart = a.wpart + (size_t)(nref & 1) * a.gstride * 64;
+        double dv = 0.0;
+        if (tc < jl) {
+            double acc[16];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc[u] = __ldcg(a.gram + (size_t)(q + u) * bw * bw + e);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) s += acc[u];
+            for (int u = 0; u < 16; ++u) {
+                const int q = tr + 4 * u;
+                acc[u] = (q < G) ? __ldcg(dpart + (size_t)q * 64 + tc) : 0.0;
             }
-            for (; q < G; ++q) s += __ldcg(a.gram + (size_t)q * bw * bw + e);
+            for (int q = tr + 64; q < G; q += 4) acc[0] += __ldcg(dpart + (size_t)q * 64 + tc);
+#pragma unroll
+            for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+                for (int u = 0; u < h; ++u) acc[u] += acc[u + h];
+            dv = acc[0];
         }
-        gsum[e] = s;
-        tloc[e] = 0.0;
-    }
-    __syncthreads();
-    for (int j = 0; j < bw; ++j) {
-        // T[0:j, j] = -tau_j * T[0:j, 0:j] * gram[0:j, j]
-        if (tid < j) {
-            double s = 0.0;
-            for (int p = tid; p < j; ++p) s += tloc[tid + p * bw] * gsum[p + j * bw];
-            tloc[tid + j * bw] = -tau_s[j] * s;
+        colpart[tr][tc] = dv;
+        __syncthreads();
+        if (tid < bw) wsum[tid] = colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
+        __syncthreads();
+        if (tid < jl) {
+            double acc = 0.0;
+            for (int q = tid; q < jl; ++q) acc += tloc[tid + q * 64] * wsum[q];
+            tloc[tid + jl * 64] = -tau_s[jl] * acc;
         }
-        if (tid == 0) tloc[j + j * bw] = tau_s[j];
+        if (tid == 0) tloc[jl + jl * 64] = tau_s[jl];
         __syncthreads();
     }
     for (int e = tid; e < bw * bw; e += blockDim.x) {
         int r = e % bw, c = e / bw;
-        Tm[(size_t)r + (size_t)c * ldt] = (T)tloc[e];
+        Tm[(size_t)r + (size_t)c * ldt] = (T)tloc[r + c * 64];
     }
 }
 
@@ -414,9 +449,11 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         // for co-residency
         int rows = 256;
         int G = ceil_div(m, rows);
-        size_t smem = (size_t)rows * (bw + 1) * sizeof(T);
-        size_t smem_t = 2 * (size_t)bw * bw * sizeof(double);
-        if (smem < smem_t) smem = smem_t;
+        // panel rows, then T (64 x 64 binary64) at the next 16-byte boundary
+        auto panel_smem = [&](int r) {
+            return (((size_t)r * (bw + 1) * sizeof(T) + 15) & ~(size_t)15) + 64 * 64 * sizeof(double);
+        };
+        size_t smem = panel_smem(rows);
         static PerDeviceOnce attr_set;  // per instantiation
         e = once_per_device(attr_set, [] {
             return cudaFuncSetAttribute(panel_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -428,8 +465,7 @@ cudaError_t sy2sb(cudaStream_t st, int n, int b, T *a, int lda, T *v1, T *t1, T 
         while (G > max_coresident || G > max_g) {
             rows *= 2;
             G = ceil_div(m, rows);
-            smem = (size_t)rows * (bw + 1) * sizeof(T);
-            if (smem < smem_t) smem = smem_t;
+            smem = panel_smem(rows);
             if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_qr_kernel<T>, 256, smem);
             max_coresident = per_sm * num_sms;
