@@ -197,7 +197,8 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
     const int L = min(b, n - r);
     const int cb = r - b;  // first column of X
     size_t pslot = slot - 1;
-    for (int i = tid; i < b; i += nt) vprev[i] = ldg_l2(v2 + pslot * b + i);
+    // the previous step's reflector, loaded in the same batch as X and D below
+    const T vp = (tid < b) ? ldg_l2(v2 + pslot * b + tid) : T(0);
     const T taup = ldg_l2(tau2 + pslot);
     // X = A[r .. r+L-1, cb .. cb+b-1]  (all strictly below the diagonal, distance 1..2b-1)
     // and D = A[r .. r+L-1]^2 (read now: the task's window is not touched by anyone else;
@@ -218,6 +219,7 @@ __device__ void chase_task(const ChaseArgs &a, T *band, T *v2, T *tau2, int j, i
             if (ti < L && c < b) X[ti + c * ld] = xr[q];
             if (ti < L && c <= ti) D[ti + c * ld] = dr[q];
         }
+        if (tid < b) vprev[tid] = vp;
     }
     __syncthreads();
     if (ti < L)

@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
     __shared__ double tau_s[64];
     __shared__ double wsum[64];
     __shared__ double colpart[4][64];
+    __shared__ double prow_s[64];  // row j of the panel (published by the CTA holding it)
     __shared__ double refl[3];  // beta, tau, 1 / (alpha - beta) of the current column
     const int g = blockIdx.x, G = gridDim.x;
     const int tid = threadIdx.x;
@@ -67,6 +68,24 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
     if (g == 0)
         for (int e = tid; e < 64 * 64; e += blockDim.x) tloc[e] = 0.0;
     __syncthreads();
+    // sum over the rows gi >= first (gi = row0 + i, i = tr, tr + 4, ...) of x_i Ploc[i][c],
+    // x_i = Ploc[i][col] (1 at gi == col when unit): four independent partial sums
+    auto col_dot = [&](int c, int col, int first, bool unit) -> T {
+        auto xv = [&](int i) -> T {
+            const int gi = row0 + i;
+            return gi < first ? T(0) : ((unit && gi == col) ? T(1) : Ploc[i * bwp + col]);
+        };
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        int i = tr;
+        for (; i + 12 < nrow; i += 16) {
+            s0 = fma(xv(i), Ploc[i * bwp + c], s0);
+            s1 = fma(xv(i + 4), Ploc[(i + 4) * bwp + c], s1);
+            s2 = fma(xv(i + 8), Ploc[(i + 8) * bwp + c], s2);
+            s3 = fma(xv(i + 12), Ploc[(i + 12) * bwp + c], s3);
+        }
+        for (; i < nrow; i += 4) s0 = fma(xv(i), Ploc[i * bwp + c], s0);
+        return (s0 + s1) + (s2 + s3);
+    };
 
     const int nref = min(bw, a.m);
     // One grid barrier per column. Before it, every CTA publishes (for column j, already
@@ -89,16 +108,9 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             const int c = tc;
             for (int i = tid; i < nrow; i += blockDim.x)
                 if (row0 + i > j) { T x = Ploc[i * bwp + j]; ss = fma(x, x, ss); }
-            if (c > j && c < bw)
-                for (int i = tr; i < nrow; i += 4)
-                    if (row0 + i > j) s = fma(Ploc[i * bwp + j], Ploc[i * bwp + c], s);
-            if (c < j - 1)  // v_c . v_(j-1) over the rows >= j - 1 (v_c is zero above c)
-                for (int i = tr; i < nrow; i += 4) {
-                    const int gi = row0 + i;
-                    if (gi < j - 1) continue;
-                    const T vj = (gi == j - 1) ? T(1) : Ploc[i * bwp + j - 1];
-                    s = fma(Ploc[i * bwp + c], vj, s);
-                }
+            if (c > j && c < bw) s = col_dot(c, j, j + 1, false);
+            // v_c . v_(j-1) over the rows >= j - 1 (v_c is zero above c)
+            if (c < j - 1) s = col_dot(c, j - 1, j - 1, true);
             colpart[tr][tc] = (double)s;
             double sst = block_sum((double)ss, red);  // also orders colpart
             if (tid < bw)
@@ -120,6 +132,8 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             // L2-coherent loads (written by other CTAs before the barrier), all issued
             // before they are summed
             // (up to 64 CTAs: all 16 loads of a thread in flight at once)
+            // row j entries c >= j, loaded with the partials (one round trip for both)
+            const double pv = (tid >= j && tid < bw) ? __ldcg(prow + tid) : 0.0;
             double dv = 0.0;
             if ((tc > j && tc < bw) || tc < j - 1) {
                 double acc[16];
@@ -136,6 +150,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
                 dv = acc[0];
             }
             colpart[tr][tc] = dv;
+            if (tid < bw) prow_s[tid] = pv;
             __syncthreads();
             if (tid < bw) wsum[tid] = colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
             // the reflector's scalars, once, in the panel's precision (one thread's
@@ -143,7 +158,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             // chip, whose binary64 units are few)
             if (tid == 0) {
                 const T sigma2 = (T)red[0];
-                const T alpha = (T)__ldcg(prow + j);
+                const T alpha = (T)prow_s[j];
                 if (sigma2 == T(0)) { refl[0] = (double)alpha; refl[1] = 0.0; refl[2] = 0.0; }
                 else {
                     const T nrm = dsqrt<T>(fma(alpha, alpha, sigma2));
@@ -167,7 +182,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             __syncthreads();
         }
         // w_c = P[j][c] + scl d_c; stored pre-multiplied by tau
-        if (tid > j && tid < bw) wsum[tid] = tau * (__ldcg(prow + tid) + scl * wsum[tid]);
+        if (tid > j && tid < bw) wsum[tid] = tau * (prow_s[tid] + scl * wsum[tid]);
         __syncthreads();
         const T sclT = (T)scl;
         for (int i = tid; i < nrow; i += blockDim.x)
@@ -177,11 +192,13 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
             const int c = tc;
             if (c > j && c < bw) {
                 const T wt = (T)wsum[c];
+#pragma unroll 4
                 for (int i = tr; i < nrow; i += 4) {
                     const int gi = row0 + i;
-                    if (gi < j) continue;
-                    const T v = (gi == j) ? T(1) : Ploc[i * bwp + j];
-                    Ploc[i * bwp + c] = fma(-v, wt, Ploc[i * bwp + c]);
+                    if (gi >= j) {
+                        const T v = (gi == j) ? T(1) : Ploc[i * bwp + j];
+                        Ploc[i * bwp + c] = fma(-v, wt, Ploc[i * bwp + c]);
+                    }
                 }
             }
         }
@@ -209,14 +226,7 @@ __global__ void __launch_bounds__(256) panel_qr_kernel(T *P, T *V, T *Tm, int ld
     const int jl = nref - 1;
     {
         double *dpart = a.wpart + (size_t)(nref & 1) * a.gstride * 64;
-        T s = T(0);
-        if (tc < jl)
-            for (int i = tr; i < nrow; i += 4) {
-                const int gi = row0 + i;
-                if (gi < jl) continue;
-                const T vj = (gi == jl) ? T(1) : Ploc[i * bwp + jl];
-                s = fma(Ploc[i * bwp + tc], vj, s);
-            }
+        const T s = (tc < jl) ? col_dot(tc, jl, jl, true) : T(0);
         colpart[tr][tc] = (double)s;
         __syncthreads();
         if (tid < bw) dpart[(size_t)g * 64 + tid] = colpart[0][tid] + colpart[1][tid] + colpart[2][tid] + colpart[3][tid];
