@@ -72,7 +72,10 @@ template <typename T> __device__ __forceinline__ T dsqrt(T x);
 template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
 
-// Block-wide sum of one value per thread (blockDim.x multiple of 32, <= 1024).
+// Block-wide sum of one value per thread (blockDim.x multiple of 32, <= 1024). Every warp
+// reduces the per-warp partials with the same shuffle tree, so all threads get the same
+// bits without a second round through shared memory; the leading barrier keeps a
+// previous call's readers of red ahead of this call's writers.
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T *red /* >= 32 entries of shared */)
 {
@@ -83,14 +86,8 @@ __device__ __forceinline__ T block_sum(T v, T *red /* >= 32 entries of shared */
     __syncthreads();
     const int nw = (blockDim.x + 31) >> 5;
     T s = (lane < nw) ? red[lane] : T(0);
-    if (warp == 0) {
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) red[0] = s;
-    }
-    __syncthreads();
-    T r = red[0];
-    __syncthreads();
-    return r;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
 }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -336,13 +336,40 @@ cudaError_t transpose(cudaStream_t st, int m, int n, const T *src, int lds, T *d
     return cudaGetLastError();
 }
 
+// upper := lower^T in place, 64 x 64 tiles (tile (bi, bj) of the lower triangle is read
+// and its transpose written to tile (bj, bi)); 256 threads, each with its 16 loads in
+// flight together (the copy is bound by HBM traffic, which needs many bytes in flight).
+template <typename T>
+__global__ void __launch_bounds__(256) mirror64_kernel(int n, T *a, int lda)
+{
+    __shared__ T tile[64][65];
+    const int bi = blockIdx.x * 64, bj = blockIdx.y * 64;
+    if (bi < bj) return;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
+    T v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int i = bi + tx, j = bj + ty + 4 * u;
+        v[u] = (i < n && j < n) ? a[(size_t)i + (size_t)j * lda] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) tile[ty + 4 * u][tx] = v[u];
+    __syncthreads();
+    // a(j, i) = a(i, j) for i > j: destination row j = bj + tx, column i = bi + r
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int r = ty + 4 * u, j = bj + tx, i = bi + r;
+        if (i < n && j < n && i > j) a[(size_t)j + (size_t)i * lda] = tile[tx][r];
+    }
+}
+
 template <typename T>
 cudaError_t mirror_lower(cudaStream_t st, int n, T *a, int lda)
 {
     if (n <= 0) return cudaSuccess;
-    dim3 grid(ceil_div(n, 32), ceil_div(n, 32)), block(32, 8);
+    dim3 grid(ceil_div(n, 64), ceil_div(n, 64));
     EGB_COUNT_LAUNCH();
-    tile_transpose_kernel<T><<<grid, block, 0, st>>>(n, n, a, lda, a, lda, 1);
+    mirror64_kernel<T><<<grid, 256, 0, st>>>(n, a, lda);
     return cudaGetLastError();
 }
 

@@ -297,14 +297,30 @@ __device__ __forceinline__ void tile_mm(const T *A, const T *B, int kmax, T (&c)
     }
 }
 
+// A 64 x 64 tile from global memory, element (i, c) = ld(i, c) stored by st(i, c, value):
+// 16 elements per thread (256 threads), all loads in flight before the first store.
+template <typename T, typename Ld, typename St>
+__device__ __forceinline__ void tile_in(Ld ld, St st)
+{
+    T v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int e = threadIdx.x + 256 * u;
+        v[u] = ld(e & 63, e >> 6);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int e = threadIdx.x + 256 * u;
+        st(e & 63, e >> 6, v[u]);
+    }
+}
+
 // tile[i][c] = src[(r0 + i) + c * ld] for i < rows, c < bw; zero elsewhere
 template <typename T>
 __device__ __forceinline__ void load_rows(T *tile, const T *src, int ld, int r0, int rows, int bw)
 {
-    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-        const int i = e & 63, c = e >> 6;
-        tile[i * kWLd + c] = (i < rows && c < bw) ? src[(size_t)(r0 + i) + (size_t)c * ld] : T(0);
-    }
+    tile_in<T>([&](int i, int c) { return (i < rows && c < bw) ? src[(size_t)(r0 + i) + (size_t)c * ld] : T(0); },
+               [&](int i, int c, T x) { tile[i * kWLd + c] = x; });
 }
 
 // X rows = Xa rows T; partial Y (64 x 64 per block, column-major) = V rows^T X rows
@@ -330,10 +346,8 @@ __global__ void __launch_bounds__(256) w_stage1_kernel(int m, int bw, const T *x
         }
     __syncthreads();
     // V rows transposed into sA: sA[a][i] = V[r0 + i][a]
-    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-        const int i = e & 63, a = e >> 6;
-        sA[a * kWLd + i] = (i < rows && a < bw) ? V[(size_t)(r0 + i) + (size_t)a * ldv] : T(0);
-    }
+    tile_in<T>([&](int i, int a) { return (i < rows && a < bw) ? V[(size_t)(r0 + i) + (size_t)a * ldv] : T(0); },
+               [&](int i, int a, T x) { sA[a * kWLd + i] = x; });
     __syncthreads();
     tile_mm(sA, sX, kWRows, c);
     T *yp = ypart + (size_t)blockIdx.x * 64 * 64;
@@ -371,11 +385,9 @@ __global__ void __launch_bounds__(256) w_stage3_kernel(int m, int bw, const T *X
     T *sA = reinterpret_cast<T *>(wsm_raw), *sB = sA + 64 * kWLd, *sZ = sB + 64 * kWLd;
     const int r0 = blockIdx.x * kWRows, rows = min(kWRows, m - r0);
     // sA = T^T (sA[a][k] = T[k][a]), sB = Y
-    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-        const int i = e & 63, c = e >> 6;
-        sA[c * kWLd + i] = (i < bw && c < bw) ? Tm[(size_t)i + (size_t)c * ldt] : T(0);
-        sB[i * kWLd + c] = Y[i + c * 64];
-    }
+    tile_in<T>([&](int i, int c) { return (i < bw && c < bw) ? Tm[(size_t)i + (size_t)c * ldt] : T(0); },
+               [&](int i, int c, T x) { sA[c * kWLd + i] = x; });
+    tile_in<T>([&](int i, int c) { return Y[i + c * 64]; }, [&](int i, int c, T x) { sB[i * kWLd + c] = x; });
     __syncthreads();
     T c[4][4];
     tile_mm(sA, sB, bw, c);
