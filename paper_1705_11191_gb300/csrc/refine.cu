@@ -463,7 +463,8 @@ int solve_fp32_refine(elsi_gb_handle_s *h, const SolveRequest &rq)
     // rest are reported at the accuracy of this route. T itself carries the binary32
     // rounding of the reduction (about 6e-8 ||T||), so bisection to 1e-8 ||T|| changes
     // neither the eigenvalues nor, through the twisted factorisations, the eigenvectors
-    // beyond that level.
+    // beyond that level. (At 1e-7 ||T|| the refinement of the 3D-cluster problem at
+    // n = 16384 no longer converges and the solve falls back to the binary64 route.)
     CKR(stebz(st, n, w.d, w.e, n, w.w, w.status, 1e-8));
     // eigenvector scratch (3 n^2 + n binary64 values) in the digit-plane buffer, free here
     CKR(stein<float>(st, n, w.d, w.e, n, w.w, X32, n, reinterpret_cast<double *>(w.oz), w.status));
