@@ -107,3 +107,60 @@ def test_spin_limit_setter(lib):
         assert lib.elsi_gb_get_spin_limit() == 5
     finally:
         assert lib.elsi_gb_set_spin_limit(old) == 0
+
+
+def _testing_protos(lib):
+    v = ctypes.c_void_p
+    lib.elsi_gb_symm_tall_f32_work.argtypes = [ctypes.c_int]
+    lib.elsi_gb_symm_tall_f32_work.restype = ctypes.c_size_t
+    lib.elsi_gb_symm_tall_f32.argtypes = [ctypes.c_int, ctypes.c_int, v, ctypes.c_int, v, ctypes.c_int,
+                                          v, ctypes.c_int, v, ctypes.c_size_t, v, v]
+    lib.elsi_gb_gemm_f64_digits_planes.argtypes = [ctypes.c_int] * 3
+    lib.elsi_gb_gemm_f64_digits_planes.restype = ctypes.c_size_t
+    lib.elsi_gb_gemm_f64_digits_exps.argtypes = [ctypes.c_int] * 2
+    lib.elsi_gb_gemm_f64_digits_exps.restype = ctypes.c_size_t
+    lib.elsi_gb_gemm_f64_digits.argtypes = (
+        [ctypes.c_int] * 5 + [ctypes.c_double, v, ctypes.c_int, v, ctypes.c_int, ctypes.c_double, v,
+                              ctypes.c_int, ctypes.c_int, ctypes.c_int, v, ctypes.c_size_t, v,
+                              ctypes.c_size_t, v, v])
+
+
+def test_testing_entry_scratch_sizes(lib):
+    """Scratch sizes of the testing entries are host arithmetic: the digit planes hold 7
+    planes of (rows padded to 128) x (K padded to 16) bf16 values per operand; the
+    symmetric panel product holds the V hi/lo planes (64 x K padded to 32 each) and at most
+    tiles_m + 3 G partial 128 x 64 tiles, G = min(256, tiles_m * k-tiles)."""
+    _testing_protos(lib)
+
+    def up(x, q):
+        return (x + q - 1) // q * q
+
+    for m, n, k in [(1, 1, 1), (200, 130, 70), (4099, 64, 40000)]:
+        assert lib.elsi_gb_gemm_f64_digits_planes(m, n, k) == 7 * (up(m, 128) + up(n, 128)) * up(k, 16)
+        assert lib.elsi_gb_gemm_f64_digits_exps(m, n) == up(m, 128) + up(n, 128)
+    for m in [1, 100, 4099, 16384]:
+        kp = up(m, 32)
+        tiles = (m + 127) // 128
+        G = min(256, tiles * (kp // 32))
+        assert lib.elsi_gb_symm_tall_f32_work(m) == 2 * 64 * kp + (tiles + 3 * G) * 128 * 64 + 64
+    assert lib.elsi_gb_symm_tall_f32_work(0) == 0
+
+
+def test_testing_entries_reject_bad_arguments(lib):
+    """Bad sizes, digit counts and missing buffers come back as ELSI_ERR_ARG (1) before any
+    CUDA call (the pointers below are never dereferenced)."""
+    _testing_protos(lib)
+    p = ctypes.c_void_p(16)
+    # symmetric panel product: nv > 64, nv < 1, m < 1, null scratch
+    assert lib.elsi_gb_symm_tall_f32(64, 65, p, 64, p, 64, p, 64, p, 1 << 20, p, None) == 1
+    assert lib.elsi_gb_symm_tall_f32(64, 0, p, 64, p, 64, p, 64, p, 1 << 20, p, None) == 1
+    assert lib.elsi_gb_symm_tall_f32(0, 8, p, 64, p, 64, p, 64, p, 1 << 20, p, None) == 1
+    assert lib.elsi_gb_symm_tall_f32(64, 8, p, 64, p, 64, p, 64, None, 1 << 20, p, None) == 1
+    # digit product: digits outside 1..7, short leading dimensions, short scratch
+    args = lambda digits, lda, pe: (0, 0, 64, 32, 48, 1.0, p, lda, p, 48, 0.0, p, 64, 0, digits,
+                                    p, pe, p, 1 << 10, p, None)
+    big = lib.elsi_gb_gemm_f64_digits_planes(64, 32, 48)
+    assert lib.elsi_gb_gemm_f64_digits(*args(0, 64, big)) == 1
+    assert lib.elsi_gb_gemm_f64_digits(*args(8, 64, big)) == 1
+    assert lib.elsi_gb_gemm_f64_digits(*args(7, 63, big)) == 1
+    assert lib.elsi_gb_gemm_f64_digits(*args(7, 64, big - 1)) == 1
